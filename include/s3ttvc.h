@@ -1,0 +1,242 @@
+/*
+ * s3ttvc.h -- C ABI of the GB300 (sm_103a) S^3TTVc library.
+ *
+ * The operation (Sec. II, Eq. 1-2): for a rank-N hypergraph H = (V, E) with
+ * edge weights w(e) = |e|, the order-N blowup tensor B has, for every edge e,
+ * the value w(e)/|beta(e)| at every N-tuple of nodes of e that uses each node
+ * of e at least once (|beta(e)| = |e|! S(N,|e|), footnote to Sec. II).  The
+ * library computes
+ *
+ *     y = B x^(N-1),   y_v = sum_{e containing v} c(e, v),
+ *     c(e, v) = |e| (N-1)! / |beta(e)| * [t^(N-1)] e^(x_v t) prod_{u in e, u != v} (e^(x_u t) - 1)
+ *
+ * which is the per-(edge, node) generating-function value of Algorithm 2,
+ * evaluated with truncated power-series products, leave-one-out prefix and
+ * suffix products (Sec. IV), or the level-by-level CCSS forest of Sec. III
+ * and Algorithm 4 (layout S3_LAYOUT_CCSS).  s3_hcentrality runs Algorithm 1
+ * (NQZ) for the H-eigenvector centrality of Sec. II.
+ *
+ * Conventions shared by every entry point
+ *   - Node ids are 0-based int32.  Hypergraphs are CSR: edge_ptr (int64, m+1
+ *     entries, edge_ptr[0] = 0, non-decreasing) and members (int32,
+ *     edge_ptr[m] entries).  The order of members inside an edge and of the
+ *     edges themselves does not matter.
+ *   - "device" pointers are CUDA global-memory pointers on the graph's device
+ *     (any allocator: cudaMalloc, PyTorch, ...); "host" pointers are ordinary
+ *     CPU memory.  The caller owns every buffer it passes; the library owns
+ *     the graph handle and everything the handle allocated.
+ *   - ``stream`` is a cudaStream_t passed as void* (NULL = legacy default
+ *     stream).  Unless stated otherwise a call only enqueues work on that
+ *     stream and returns; results are ready when the stream is.
+ *   - Every entry point returns an s3_status and never aborts.  On failure
+ *     s3_last_error() returns a message for the calling thread; outputs are
+ *     then unspecified.
+ *   - A graph handle may be used by one host thread at a time, and calls that
+ *     share a handle must be ordered on one stream (the handle owns scratch
+ *     memory that every call reuses).
+ */
+#ifndef S3TTVC_H
+#define S3TTVC_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define S3_VERSION 1
+#define S3_MAX_RANK 128
+
+typedef enum {
+    S3_OK = 0,
+    S3_EINVAL = 1,    /* invalid argument or malformed hypergraph */
+    S3_ENOMEM = 2,    /* device or host allocation failed */
+    S3_ECUDA = 3,     /* a CUDA call failed (message in s3_last_error) */
+    S3_ENOCONV = 4,   /* NQZ did not reach the tolerance within max_iter */
+    S3_ETIMEOUT = 5,  /* a bounded device wait gave up */
+    S3_ERANGE = 6,    /* results left the range of the arithmetic type */
+    S3_ENOTSUP = 7    /* configuration not supported by this build */
+} s3_status;
+
+typedef enum { S3_F32 = 0, S3_F64 = 1 } s3_dtype;
+
+typedef enum {
+    /* y_v is summed node by node from a per-(edge, node) buffer laid out in
+     * node-sorted incidence order: deterministic, bit-identical run to run. */
+    S3_REDUCE_SEGMENTED = 0,
+    /* contributions are added with warp-aggregated atomics; the FP32 path
+     * keeps a two-sum compensation term per node that is folded in at the
+     * end.  Summation order (hence rounding) varies run to run. */
+    S3_REDUCE_ATOMIC = 1
+} s3_reduce;
+
+typedef enum {
+    /* each edge recomputes its own prefix and suffix products (Sec. IV with
+     * the leave-one-out identity E = Ebar + 1) */
+    S3_LAYOUT_EDGE = 0,
+    /* the trimmed CCSS forest of Sec. III evaluated level by level: every
+     * forest node multiplies its parent's truncated product by one series
+     * (the memoisation of Algorithm 4) and every special leaf (e, v) takes a
+     * dot product with E_N(x_v) */
+    S3_LAYOUT_CCSS = 1
+} s3_layout;
+
+typedef struct {
+    int32_t rank;          /* N; 0 = largest edge size.  Must be >= largest edge size, <= S3_MAX_RANK */
+    int32_t reduce;        /* s3_reduce */
+    int32_t layout;        /* s3_layout used by s3_sttsvc */
+    int32_t build_ccss;    /* 1 = also build the CCSS forest (implied by layout = CCSS) */
+    int32_t device;        /* CUDA device ordinal; -1 = the calling thread's current device */
+    int32_t thread_max_w;  /* edges whose window N-|e|+1 is <= this use one thread per edge, wider ones
+                              one warp per edge; 0 = library default (32), range 1..32 */
+    int32_t block_threads; /* threads per block of the thread-per-edge kernels; 0 = default (128) */
+    int32_t reserved[9];
+} s3_options;
+
+typedef struct s3_graph_s *s3_graph_t;
+
+/* Host-side description of a built format (s3_format_inspect / s3_graph_query). */
+typedef struct {
+    int64_t n, m, nnz;                 /* nodes, edges, sum of edge sizes */
+    int32_t rank;                      /* N */
+    int32_t max_edge;                  /* largest edge size */
+    int64_t max_degree;                /* largest node degree */
+    int64_t edges_per_size[S3_MAX_RANK + 1];   /* bucket sizes, index = |e| */
+    int64_t ccss_levels;               /* number of non-empty CCSS levels (0 if not built) */
+    int64_t ccss_nodes_per_level[S3_MAX_RANK + 1]; /* trimmed forest, index = level (1-based) */
+    int64_t ccss_nodes;                /* total forest nodes */
+    int64_t ccss_special_leaves;       /* = nnz */
+    int64_t ccss_products;             /* series products (one per forest node at level >= 2) */
+    int64_t device_bytes;              /* device memory held by the handle (0 for inspect) */
+} s3_format_info;
+
+/* Fill *opt with defaults (rank 0, segmented reduce, edge layout, current device). */
+s3_status s3_options_init(s3_options *opt);
+
+/*
+ * Validate and lay out a hypergraph on the host without touching any GPU
+ * (no CUDA call is made).  Checks: n >= 1, m >= 0, edge_ptr[0] = 0 and
+ * non-decreasing, every edge non-empty, ids in [0, n), no node repeated inside
+ * an edge, rank >= largest edge size, rank <= S3_MAX_RANK, edge_ptr[m] < 2^31.
+ * Returns S3_EINVAL with a message if a check fails.  With opt->build_ccss
+ * (or layout CCSS) the trimmed CCSS forest of Sec. III is built and counted.
+ * edge_ptr, members: host.  info: host, written on success.
+ */
+s3_status s3_format_inspect(int64_t n, int64_t m, const int64_t *edge_ptr, const int32_t *members,
+                            const s3_options *opt, s3_format_info *info);
+
+/*
+ * Build the device format (Sec. III layouts) and return a handle in *out.
+ * Performs the checks of s3_format_inspect, sorts every edge (index-ordered
+ * form, footnote to Sec. II-B), buckets edges by size, builds the
+ * node-sorted incidence used by the deterministic reduce and (if requested)
+ * the CCSS forest, then uploads everything once and allocates the handle's
+ * scratch memory.  Synchronous.  edge_ptr, members: host, only read.
+ */
+s3_status s3_build_format(int64_t n, int64_t m, const int64_t *edge_ptr, const int32_t *members,
+                          const s3_options *opt, s3_graph_t *out);
+
+/* Describe a built handle.  info: host. */
+s3_status s3_graph_query(s3_graph_t g, s3_format_info *info);
+
+/*
+ * y = B x^(N-1) (Eq. 1).  x: device, n elements of dt (float or double).
+ * y: device, n elements of dt, overwritten.  x and y must not overlap.
+ * Arithmetic is in dt throughout the series products; per edge the vector is
+ * rescaled by an exact power of two before the products and the result is
+ * rescaled back, so intermediate terms stay in range.  Results that underflow
+ * or overflow dt are counted (s3_range_events) but not reported here.
+ * Uses the handle's layout and reduce mode.
+ */
+s3_status s3_sttsvc(s3_graph_t g, s3_dtype dt, const void *x, void *y, void *stream);
+
+/* As s3_sttsvc with an explicit layout (s3_layout); CCSS needs a handle built with the forest. */
+s3_status s3_sttsvc_layout(s3_graph_t g, s3_dtype dt, int32_t layout, const void *x, void *y, void *stream);
+
+/*
+ * End-to-end variant: x_host and y_host are HOST buffers (n elements of dt,
+ * pinned memory recommended).  Copies x to the device, computes as
+ * s3_sttsvc, copies y back and synchronises ``stream`` before returning.
+ */
+s3_status s3_sttsvc_host(s3_graph_t g, s3_dtype dt, const void *x_host, void *y_host, void *stream);
+
+/* Device time of one s3_sttsvc call, split into the per-edge series kernels and the reduce. */
+typedef struct {
+    float edge_ms;     /* all per-edge (size bucket) kernels */
+    float reduce_ms;   /* segmented reduce, or the compensation pass of the atomic mode */
+    float total_ms;
+    int32_t launches;  /* kernels launched by the call */
+    int32_t reserved[4];
+} s3_profile;
+
+/*
+ * Run s3_sttsvc once (edge layout) with CUDA events recorded on ``stream``
+ * before the edge kernels, between them and the reduce, and after the
+ * reduce; synchronises ``stream`` and writes the elapsed times to *prof
+ * (host).  Arguments as s3_sttsvc.
+ */
+s3_status s3_sttsvc_profile(s3_graph_t g, s3_dtype dt, const void *x, void *y, s3_profile *prof, void *stream);
+
+/*
+ * Number of per-(edge, node) results since the handle was built (or since the
+ * last reset) that came out as zero, subnormal or non-finite although their
+ * exact value is a positive normal number of the call's type.  Synchronises
+ * the handle's device.  reset != 0 clears the counter.  count: host.
+ */
+s3_status s3_range_events(s3_graph_t g, int64_t *count, int32_t reset);
+
+/* ------------------------------------------------------------------ NQZ --- */
+
+typedef struct {
+    double tol;            /* stop when (lambda_max - lambda_min)/lambda_min < tol (Algorithm 1) */
+    int32_t max_iter;      /* passes through the repeat body; <= 0 = 10000 */
+    int32_t precision;     /* 0 = FP64 throughout; 1 = FP32 series until the gap is below
+                              switch_tol (or stops shrinking), then FP64 to tol */
+    double switch_tol;     /* FP32 -> FP64 hand-over gap for precision 1; <= 0 = 1e-5 */
+    int32_t check_every;   /* iterations per captured CUDA graph between host checks; <= 0 = 8 */
+    int32_t reserved[7];
+} s3_nqz_options;
+
+typedef struct {
+    double lambda_min, lambda_max;  /* bracket of the H-eigenvalue at the last iteration */
+    int32_t iters;                  /* passes through the repeat body (all precisions) */
+    int32_t iters_fp32;             /* of which in FP32 */
+    int32_t converged;              /* 1 if the gap reached tol */
+    int32_t reserved;
+    double seconds;                 /* wall time of the call */
+} s3_nqz_result;
+
+s3_status s3_nqz_options_init(s3_nqz_options *opt);
+
+/*
+ * H-eigenvector centrality by Algorithm 1 (NQZ) on the device.
+ * x0: device, n doubles, positive (NULL = the uniform start of Algorithm 1).
+ * x_out: device, n doubles, written with the last iterate (1-norm 1).
+ * res: host.  Every node must belong to at least one edge (S3_EINVAL
+ * otherwise: the ratio z/x^(N-1) is undefined there), and rank >= 2.
+ * FP64 is used for the (N-1)-th roots, the 1-norm, the min/max ratios and the
+ * test.  Synchronous on ``stream``; returns S3_ENOCONV (x_out and res still
+ * written) if max_iter passes do not reach tol.
+ */
+s3_status s3_hcentrality(s3_graph_t g, const s3_nqz_options *opt, const double *x0, double *x_out,
+                         s3_nqz_result *res, void *stream);
+
+/* ------------------------------------------------------------- cleanup --- */
+
+/* Release the handle and its device memory (synchronises its device).  NULL is allowed. */
+s3_status s3_destroy(s3_graph_t g);
+
+/* Message for the last failing call on this host thread ("" if none). */
+const char *s3_last_error(void);
+
+/* Constant name of a status code. */
+const char *s3_status_string(s3_status st);
+
+/* S3_VERSION of the built library. */
+int32_t s3_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* S3TTVC_H */

@@ -2,7 +2,7 @@
 
 Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
 ``bench.py`` may import or run anything in this package.  It shares no code
-with the CUDA path (``paper_2311_08595_gb300``) and never imports it.
+with the CUDA path and never imports it.
 
 Contents
   exact      -- exact rational brute force (Eq. 2 over every tensor entry),

@@ -1,0 +1,207 @@
+"""GB300 (sm_103a) S^3TTVc: sparse symmetric tensor times same vector on the
+blowup tensor of a non-uniform hypergraph, and H-eigenvector centrality.
+
+Thin Python binding of the C ABI in ``include/s3ttvc.h``.  Each function has
+the name of the entry point it calls; arguments are marshalled (PyTorch CUDA
+tensors or numpy arrays to raw pointers, streams to ``cudaStream_t``) and
+every step of the computation runs in the library's CUDA kernels.  There is
+no CPU fallback: without the built library the import of any entry point
+raises.
+
+    import paper_2311_08595_gb300 as s3
+    g = s3.s3_build_format(n, edge_ptr, members)           # numpy CSR
+    s3.s3_sttsvc(g, x, y)                                   # torch.cuda tensors
+    x_c, res = s3.s3_hcentrality(g, tol=1e-8, precision=1)
+"""
+from __future__ import annotations
+
+import ctypes
+
+import numpy as np
+
+from . import _lib
+from ._lib import (S3_F32, S3_F64, S3_LAYOUT_CCSS, S3_LAYOUT_EDGE, S3_REDUCE_ATOMIC,  # noqa: F401
+                   S3_REDUCE_SEGMENTED, S3Error, check, load, ptr)
+
+__all__ = [
+    "Graph", "S3Error", "s3_options_init", "s3_format_inspect", "s3_build_format", "s3_graph_query",
+    "s3_sttsvc", "s3_sttsvc_layout", "s3_sttsvc_host", "s3_sttsvc_profile", "s3_range_events", "s3_hcentrality",
+    "s3_nqz_options_init", "s3_destroy", "s3_version", "lib_path",
+]
+
+
+def lib_path():
+    return _lib.LIB_PATH
+
+
+def s3_version():
+    return int(load().s3_version())
+
+
+def s3_options_init(**kw):
+    """Default s3_options, with any field overridden by keyword."""
+    o = _lib.s3_options()
+    check(load().s3_options_init(ctypes.byref(o)))
+    for k, v in kw.items():
+        if not hasattr(o, k):
+            raise TypeError(f"unknown option {k}")
+        setattr(o, k, int(v))
+    return o
+
+
+def _csr(edge_ptr, members):
+    ep = np.ascontiguousarray(edge_ptr, dtype=np.int64)
+    mem = np.ascontiguousarray(members, dtype=np.int32)
+    return ep, mem
+
+
+def _info_dict(info):
+    d = {f: getattr(info, f) for f, _ in info._fields_}
+    d["edges_per_size"] = list(info.edges_per_size)
+    d["ccss_nodes_per_level"] = list(info.ccss_nodes_per_level)
+    return d
+
+
+def s3_format_inspect(n, edge_ptr, members, opt=None, **kw):
+    """Validate/lay out on the host only (no GPU); returns the s3_format_info as a dict."""
+    ep, mem = _csr(edge_ptr, members)
+    o = opt or s3_options_init(**kw)
+    info = _lib.s3_format_info()
+    check(load().s3_format_inspect(int(n), ep.size - 1, ep.ctypes.data, mem.ctypes.data,
+                                   ctypes.byref(o), ctypes.byref(info)))
+    return _info_dict(info)
+
+
+class Graph:
+    """Owns an s3_graph_t; released by s3_destroy (or when garbage-collected)."""
+
+    def __init__(self, handle, n, rank, opt):
+        self.handle = handle
+        self.n = n
+        self.rank = rank
+        self.opt = opt
+
+    def __del__(self):
+        try:
+            s3_destroy(self)
+        except Exception:
+            pass
+
+
+def s3_build_format(n, edge_ptr, members, opt=None, **kw):
+    ep, mem = _csr(edge_ptr, members)
+    o = opt or s3_options_init(**kw)
+    h = ctypes.c_void_p()
+    check(load().s3_build_format(int(n), ep.size - 1, ep.ctypes.data, mem.ctypes.data,
+                                 ctypes.byref(o), ctypes.byref(h)))
+    g = Graph(h, int(n), None, o)
+    g.rank = s3_graph_query(g)["rank"]
+    return g
+
+
+def s3_graph_query(g):
+    info = _lib.s3_format_info()
+    check(load().s3_graph_query(g.handle, ctypes.byref(info)))
+    return _info_dict(info)
+
+
+def _dtype_code(t):
+    import torch
+    if t.dtype == torch.float32:
+        return S3_F32
+    if t.dtype == torch.float64:
+        return S3_F64
+    raise TypeError("x must be float32 or float64")
+
+
+def _stream(stream):
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    return getattr(stream, "cuda_stream", stream)
+
+
+def _check_vec(g, t, name):
+    if not t.is_cuda or not t.is_contiguous() or t.numel() != g.n:
+        raise ValueError(f"{name} must be a contiguous CUDA tensor of {g.n} elements")
+
+
+def s3_sttsvc(g, x, y, stream=None):
+    """y = B x^(N-1) on the device (x, y: CUDA tensors of the same float dtype)."""
+    _check_vec(g, x, "x")
+    _check_vec(g, y, "y")
+    if x.dtype != y.dtype:
+        raise TypeError("x and y must have the same dtype")
+    check(load().s3_sttsvc(g.handle, _dtype_code(x), ptr(x), ptr(y), _stream(stream)))
+    return y
+
+
+def s3_sttsvc_layout(g, layout, x, y, stream=None):
+    _check_vec(g, x, "x")
+    _check_vec(g, y, "y")
+    check(load().s3_sttsvc_layout(g.handle, _dtype_code(x), int(layout), ptr(x), ptr(y), _stream(stream)))
+    return y
+
+
+def s3_sttsvc_host(g, x_host, y_host, stream=None):
+    """Host buffers in and out (torch CPU tensors, pinned recommended, or numpy)."""
+    if isinstance(x_host, np.ndarray):
+        code = S3_F32 if x_host.dtype == np.float32 else S3_F64
+        xp, yp = x_host.ctypes.data, y_host.ctypes.data
+    else:
+        code = _dtype_code(x_host)
+        xp, yp = x_host.data_ptr(), y_host.data_ptr()
+    check(load().s3_sttsvc_host(g.handle, code, xp, yp, _stream(stream)))
+    return y_host
+
+
+def s3_sttsvc_profile(g, x, y, stream=None):
+    """One S^3TTVc call with device timings of its phases (synchronises); returns a dict."""
+    _check_vec(g, x, "x")
+    _check_vec(g, y, "y")
+    prof = _lib.s3_profile()
+    check(load().s3_sttsvc_profile(g.handle, _dtype_code(x), ptr(x), ptr(y), ctypes.byref(prof), _stream(stream)))
+    return {"edge_ms": prof.edge_ms, "reduce_ms": prof.reduce_ms, "total_ms": prof.total_ms,
+            "launches": prof.launches}
+
+
+def s3_range_events(g, reset=False):
+    c = ctypes.c_int64()
+    check(load().s3_range_events(g.handle, ctypes.byref(c), int(bool(reset))))
+    return int(c.value)
+
+
+def s3_nqz_options_init(**kw):
+    o = _lib.s3_nqz_options()
+    check(load().s3_nqz_options_init(ctypes.byref(o)))
+    for k, v in kw.items():
+        if not hasattr(o, k):
+            raise TypeError(f"unknown NQZ option {k}")
+        setattr(o, k, v)
+    return o
+
+
+def s3_hcentrality(g, x0=None, x_out=None, stream=None, raise_on_noconv=True, **kw):
+    """Algorithm 1 (NQZ) on the device.  Returns (x_out, result dict)."""
+    import torch
+    o = s3_nqz_options_init(**kw)
+    if x_out is None:
+        x_out = torch.empty(g.n, dtype=torch.float64, device="cuda")
+    _check_vec(g, x_out, "x_out")
+    if x0 is not None:
+        _check_vec(g, x0, "x0")
+        if x0.dtype != torch.float64:
+            raise TypeError("x0 must be float64")
+    res = _lib.s3_nqz_result()
+    st = load().s3_hcentrality(g.handle, ctypes.byref(o), ptr(x0), ptr(x_out), ctypes.byref(res), _stream(stream))
+    out = {f: getattr(res, f) for f, _ in res._fields_ if f != "reserved"}
+    out["status"] = _lib.status_name(st)
+    if st != _lib.S3_OK and not (st == _lib.S3_ENOCONV and not raise_on_noconv):
+        check(st)
+    return x_out, out
+
+
+def s3_destroy(g):
+    if g is not None and getattr(g, "handle", None):
+        h, g.handle = g.handle, None
+        check(load().s3_destroy(h))

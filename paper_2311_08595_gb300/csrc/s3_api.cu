@@ -1,0 +1,357 @@
+// C ABI entry points: handles, format upload, S^3TTVc orchestration.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstring>
+#include <mutex>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "s3_graph.h"
+
+namespace s3 {
+
+namespace {
+thread_local std::string g_last_error;
+}
+
+void set_error(const std::string &msg) { g_last_error = msg; }
+
+s3_status fail(s3_status st, const std::string &msg) {
+    g_last_error = msg;
+    return st;
+}
+
+s3_status cuda_fail(cudaError_t e, const char *what) {
+    cudaGetLastError();
+    return fail(S3_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+s3_status prepare_device(int dev) {
+    static std::mutex mu;
+    static std::vector<char> done;
+    std::lock_guard<std::mutex> lock(mu);
+    if ((int)done.size() <= dev) done.resize(dev + 1, 0);
+    if (done[dev]) return S3_OK;
+    S3_CUDA(prepare_edge_kernels_f32());
+    S3_CUDA(prepare_edge_kernels_f64());
+    done[dev] = 1;
+    return S3_OK;
+}
+
+namespace {
+
+template <typename T>
+s3_status upload(s3_graph_s *g, T **dst, const std::vector<T> &src) {
+    s3_status st = dev_alloc(g, dst, src.size());
+    if (st != S3_OK) return st;
+    if (!src.empty()) S3_CUDA(cudaMemcpy(*dst, src.data(), src.size() * sizeof(T), cudaMemcpyHostToDevice));
+    return S3_OK;
+}
+
+void free_all(s3_graph_s *g) {
+    for (void *p : g->allocations) cudaFree(p);
+    g->allocations.clear();
+}
+
+}  // namespace
+
+// Launch the per-bucket edge kernels and the reduce for one call.
+s3_status run_edges(s3_graph_s *g, s3_dtype dt, const void *x, void *y, int bias, const int32_t *skip,
+                    cudaStream_t st, cudaEvent_t mid) {
+    int launches = 0;
+    const bool seg = g->opt.reduce == S3_REDUCE_SEGMENTED;
+    const size_t esz = dt == S3_F32 ? 4 : 8;
+    EdgeOutArgs o{};
+    o.bias = bias;
+    o.range_events = g->d_range;
+    o.skip = skip;
+    if (seg) {
+        o.out = g->d_buf;
+        o.mode = kOutBuffer;
+    } else {
+        o.out = y;
+        o.mode = dt == S3_F32 ? kOutAtomicComp : kOutAtomic;
+        o.comp = g->d_comp;
+        S3_CUDA(cudaMemsetAsync(y, 0, esz * (size_t)g->n, st));
+        if (dt == S3_F32) S3_CUDA(cudaMemsetAsync(g->d_comp, 0, sizeof(float) * (size_t)g->n, st));
+    }
+    for (size_t k = 0; k < g->buckets.size(); ++k) {
+        const HostBucket &hb = g->buckets[k];
+        EdgeBucketArgs b{};
+        b.ids = g->d_ids + hb.offset;
+        b.slot = g->d_slot + hb.offset;
+        b.m = hb.m;
+        b.ld = hb.ld;
+        b.s = hb.s;
+        b.N = g->N;
+        b.target = g->target[k];
+        b.K = g->K[k];
+        b.Km = g->Km[k];
+        b.Ke = g->Ke[k];
+        cudaError_t e = dt == S3_F32
+                            ? launch_edge_bucket_f32(b, (const float *)x, o, g->opt.thread_max_w, g->opt.block_threads, st)
+                            : launch_edge_bucket_f64(b, (const double *)x, o, g->opt.thread_max_w, g->opt.block_threads, st);
+        if (e != cudaSuccess) return cuda_fail(e, "edge kernel launch");
+        if (hb.m > 0) ++launches;
+    }
+    if (mid) S3_CUDA(cudaEventRecord(mid, st));
+    if (seg) {
+        ReduceArgs r{};
+        r.inc_ptr = g->d_inc_ptr;
+        r.small_nodes = g->d_small;
+        r.n_small = g->n_small;
+        r.med_nodes = g->d_med;
+        r.n_med = g->n_med;
+        r.piece_start = g->d_piece_start;
+        r.piece_len = g->d_piece_len;
+        r.n_pieces = g->n_pieces;
+        r.big_nodes = g->d_big_nodes;
+        r.big_piece_ptr = g->d_big_piece_ptr;
+        r.n_big = g->n_big;
+        r.partial = g->d_partial;
+        r.skip = skip;
+        cudaError_t e = dt == S3_F32 ? launch_reduce_f32(r, (const float *)g->d_buf, (float *)y, st)
+                                     : launch_reduce_f64(r, (const double *)g->d_buf, (double *)y, st);
+        if (e != cudaSuccess) return cuda_fail(e, "reduce launch");
+        launches += 1 + (g->n_big > 0 ? 1 : 0);
+    } else if (dt == S3_F32) {
+        cudaError_t e = launch_add_comp((float *)y, g->d_comp, g->n, skip, st);
+        if (e != cudaSuccess) return cuda_fail(e, "compensation launch");
+        ++launches;
+    }
+    g->last_launches = launches;
+    return S3_OK;
+}
+
+}  // namespace s3
+
+using namespace s3;
+
+extern "C" {
+
+s3_status s3_options_init(s3_options *opt) {
+    if (!opt) return fail(S3_EINVAL, "opt is NULL");
+    std::memset(opt, 0, sizeof(*opt));
+    opt->rank = 0;
+    opt->reduce = S3_REDUCE_SEGMENTED;
+    opt->layout = S3_LAYOUT_EDGE;
+    opt->build_ccss = 0;
+    opt->device = -1;
+    opt->thread_max_w = 0;
+    opt->block_threads = 0;
+    return S3_OK;
+}
+
+s3_status s3_format_inspect(int64_t n, int64_t m, const int64_t *edge_ptr, const int32_t *members,
+                            const s3_options *opt, s3_format_info *info) {
+    if (!info) return fail(S3_EINVAL, "info is NULL");
+    s3_options o;
+    if (opt) o = *opt;
+    else s3_options_init(&o);
+    try {
+        HostFormat f;
+        s3_status st = build_host_format(n, m, edge_ptr, members, o, f);
+        if (st != S3_OK) return st;
+        fill_info(f, info);
+        return S3_OK;
+    } catch (const std::bad_alloc &) {
+        return fail(S3_ENOMEM, "host allocation failed");
+    }
+}
+
+s3_status s3_build_format(int64_t n, int64_t m, const int64_t *edge_ptr, const int32_t *members,
+                          const s3_options *opt, s3_graph_t *out) {
+    if (!out) return fail(S3_EINVAL, "out is NULL");
+    *out = nullptr;
+    s3_options o;
+    if (opt) o = *opt;
+    else s3_options_init(&o);
+    if (o.reduce != S3_REDUCE_SEGMENTED && o.reduce != S3_REDUCE_ATOMIC) return fail(S3_EINVAL, "bad reduce mode");
+    if (o.layout != S3_LAYOUT_EDGE && o.layout != S3_LAYOUT_CCSS) return fail(S3_EINVAL, "bad layout");
+    if (o.thread_max_w < 0 || o.thread_max_w > 32) return fail(S3_EINVAL, "thread_max_w must be in 0..32");
+    if (o.block_threads < 0 || o.block_threads > 256 || o.block_threads % 32) return fail(S3_EINVAL, "block_threads must be a multiple of 32 up to 256");
+    HostFormat f;
+    try {
+        s3_status st = build_host_format(n, m, edge_ptr, members, o, f);
+        if (st != S3_OK) return st;
+    } catch (const std::bad_alloc &) {
+        return fail(S3_ENOMEM, "host allocation failed");
+    }
+    int dev = o.device;
+    if (dev < 0) S3_CUDA(cudaGetDevice(&dev));
+    DeviceGuard guard(dev);
+    s3_status st = prepare_device(dev);
+    if (st != S3_OK) return st;
+
+    s3_graph_s *g = new (std::nothrow) s3_graph_s();
+    if (!g) return fail(S3_ENOMEM, "host allocation failed");
+    g->device = dev;
+    g->opt = o;
+    g->n = f.n;
+    g->m = f.m;
+    g->nnz = f.nnz;
+    g->N = f.N;
+    fill_info(f, &g->info);
+    g->buckets = f.buckets;
+    for (const HostBucket &b : f.buckets) {
+        double K = scale_K(b.s, f.N);
+        g->K.push_back(K);
+        int e = 0;
+        double mant = std::frexp(K, &e);
+        g->Km.push_back((float)mant);
+        g->Ke.push_back(e);
+        g->target.push_back(scale_target(b.s, f.N));
+    }
+    auto bail = [&](s3_status s) {
+        free_all(g);
+        delete g;
+        return s;
+    };
+    if ((st = upload(g, &g->d_ids, f.ids)) != S3_OK) return bail(st);
+    if ((st = upload(g, &g->d_slot, f.slot)) != S3_OK) return bail(st);
+    if ((st = upload(g, &g->d_inc_ptr, f.inc_ptr)) != S3_OK) return bail(st);
+    if ((st = upload(g, &g->d_small, f.red_small)) != S3_OK) return bail(st);
+    if ((st = upload(g, &g->d_med, f.red_med)) != S3_OK) return bail(st);
+    if ((st = upload(g, &g->d_big_nodes, f.big_node)) != S3_OK) return bail(st);
+    if ((st = upload(g, &g->d_big_piece_ptr, f.big_piece_ptr)) != S3_OK) return bail(st);
+    if ((st = upload(g, &g->d_piece_start, f.piece_start)) != S3_OK) return bail(st);
+    if ((st = upload(g, &g->d_piece_len, f.piece_len)) != S3_OK) return bail(st);
+    g->n_small = (int64_t)f.red_small.size();
+    g->n_med = (int64_t)f.red_med.size();
+    g->n_big = (int64_t)f.big_node.size();
+    g->n_pieces = (int64_t)f.piece_start.size();
+    double *dd = nullptr;
+    if ((st = dev_alloc(g, &dd, (size_t)f.nnz)) != S3_OK) return bail(st);
+    g->d_buf = dd;
+    if ((st = dev_alloc(g, &dd, (size_t)g->n_pieces)) != S3_OK) return bail(st);
+    g->d_partial = dd;
+    if ((st = dev_alloc(g, &g->d_comp, (size_t)f.n)) != S3_OK) return bail(st);
+    if ((st = dev_alloc(g, &g->d_range, 1)) != S3_OK) return bail(st);
+    if (cudaMemset(g->d_range, 0, sizeof(unsigned long long)) != cudaSuccess) return bail(cuda_fail(cudaGetLastError(), "memset"));
+    if ((st = dev_alloc(g, &dd, (size_t)f.n)) != S3_OK) return bail(st);
+    g->d_xh = dd;
+    if ((st = dev_alloc(g, &dd, (size_t)f.n)) != S3_OK) return bail(st);
+    g->d_yh = dd;
+    if (f.has_ccss) {
+        if ((st = upload_ccss(g, f)) != S3_OK) return bail(st);
+    }
+    g->info.device_bytes = g->device_bytes;
+    *out = g;
+    return S3_OK;
+}
+
+s3_status s3_graph_query(s3_graph_t g, s3_format_info *info) {
+    if (!g || !info) return fail(S3_EINVAL, "NULL argument");
+    *info = g->info;
+    info->device_bytes = g->device_bytes;
+    return S3_OK;
+}
+
+s3_status s3_sttsvc_layout(s3_graph_t g, s3_dtype dt, int32_t layout, const void *x, void *y, void *stream) {
+    if (!g) return fail(S3_EINVAL, "graph is NULL");
+    if (dt != S3_F32 && dt != S3_F64) return fail(S3_EINVAL, "bad dtype");
+    if (!x || !y) return fail(S3_EINVAL, "x or y is NULL");
+    const size_t esz = dt == S3_F32 ? 4 : 8;
+    const char *xb = (const char *)x, *yb = (const char *)y;
+    if (xb < yb + esz * g->n && yb < xb + esz * g->n) return fail(S3_EINVAL, "x and y overlap");
+    DeviceGuard guard(g->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    if (layout == S3_LAYOUT_EDGE) return run_edges(g, dt, x, y, 0, nullptr, st);
+    if (layout == S3_LAYOUT_CCSS) {
+        if (!g->has_ccss) return fail(S3_EINVAL, "handle was built without the CCSS forest");
+        return run_ccss(g, dt, x, y, 0, nullptr, st);
+    }
+    return fail(S3_EINVAL, "bad layout");
+}
+
+s3_status s3_sttsvc(s3_graph_t g, s3_dtype dt, const void *x, void *y, void *stream) {
+    if (!g) return fail(S3_EINVAL, "graph is NULL");
+    return s3_sttsvc_layout(g, dt, g->opt.layout, x, y, stream);
+}
+
+s3_status s3_sttsvc_host(s3_graph_t g, s3_dtype dt, const void *x_host, void *y_host, void *stream) {
+    if (!g) return fail(S3_EINVAL, "graph is NULL");
+    if (!x_host || !y_host) return fail(S3_EINVAL, "x or y is NULL");
+    if (dt != S3_F32 && dt != S3_F64) return fail(S3_EINVAL, "bad dtype");
+    DeviceGuard guard(g->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    const size_t bytes = (dt == S3_F32 ? 4 : 8) * (size_t)g->n;
+    S3_CUDA(cudaMemcpyAsync(g->d_xh, x_host, bytes, cudaMemcpyHostToDevice, st));
+    s3_status s = s3_sttsvc(g, dt, g->d_xh, g->d_yh, stream);
+    if (s != S3_OK) return s;
+    S3_CUDA(cudaMemcpyAsync(y_host, g->d_yh, bytes, cudaMemcpyDeviceToHost, st));
+    S3_CUDA(cudaStreamSynchronize(st));
+    return S3_OK;
+}
+
+s3_status s3_sttsvc_profile(s3_graph_t g, s3_dtype dt, const void *x, void *y, s3_profile *prof, void *stream) {
+    if (!g || !prof) return fail(S3_EINVAL, "NULL argument");
+    if (dt != S3_F32 && dt != S3_F64) return fail(S3_EINVAL, "bad dtype");
+    if (!x || !y) return fail(S3_EINVAL, "x or y is NULL");
+    if (g->opt.layout != S3_LAYOUT_EDGE) return fail(S3_ENOTSUP, "profiling covers the edge layout");
+    DeviceGuard guard(g->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    cudaEvent_t ev[3];
+    for (auto &e : ev) S3_CUDA(cudaEventCreate(&e));
+    struct Cleanup {
+        cudaEvent_t *e;
+        ~Cleanup() {
+            for (int i = 0; i < 3; ++i) cudaEventDestroy(e[i]);
+        }
+    } cleanup{ev};
+    S3_CUDA(cudaEventRecord(ev[0], st));
+    s3_status s = run_edges(g, dt, x, y, 0, nullptr, st, ev[1]);
+    if (s != S3_OK) return s;
+    S3_CUDA(cudaEventRecord(ev[2], st));
+    S3_CUDA(cudaEventSynchronize(ev[2]));
+    std::memset(prof, 0, sizeof(*prof));
+    S3_CUDA(cudaEventElapsedTime(&prof->edge_ms, ev[0], ev[1]));
+    S3_CUDA(cudaEventElapsedTime(&prof->reduce_ms, ev[1], ev[2]));
+    S3_CUDA(cudaEventElapsedTime(&prof->total_ms, ev[0], ev[2]));
+    prof->launches = g->last_launches;
+    return S3_OK;
+}
+
+s3_status s3_range_events(s3_graph_t g, int64_t *count, int32_t reset) {
+    if (!g || !count) return fail(S3_EINVAL, "NULL argument");
+    DeviceGuard guard(g->device);
+    S3_CUDA(cudaDeviceSynchronize());
+    unsigned long long c = 0;
+    S3_CUDA(cudaMemcpy(&c, g->d_range, sizeof(c), cudaMemcpyDeviceToHost));
+    *count = (int64_t)c;
+    if (reset) S3_CUDA(cudaMemset(g->d_range, 0, sizeof(c)));
+    return S3_OK;
+}
+
+s3_status s3_destroy(s3_graph_t g) {
+    if (!g) return S3_OK;
+    {
+        DeviceGuard guard(g->device);
+        cudaDeviceSynchronize();
+        free_all(g);
+    }
+    delete g;
+    return S3_OK;
+}
+
+const char *s3_last_error(void) { return g_last_error.c_str(); }
+
+const char *s3_status_string(s3_status st) {
+    switch (st) {
+        case S3_OK: return "S3_OK";
+        case S3_EINVAL: return "S3_EINVAL";
+        case S3_ENOMEM: return "S3_ENOMEM";
+        case S3_ECUDA: return "S3_ECUDA";
+        case S3_ENOCONV: return "S3_ENOCONV";
+        case S3_ETIMEOUT: return "S3_ETIMEOUT";
+        case S3_ERANGE: return "S3_ERANGE";
+        case S3_ENOTSUP: return "S3_ENOTSUP";
+    }
+    return "S3_UNKNOWN";
+}
+
+int32_t s3_version(void) { return S3_VERSION; }
+
+}  // extern "C"

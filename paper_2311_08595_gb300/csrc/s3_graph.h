@@ -1,0 +1,117 @@
+// The graph handle (internal).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "s3_internal.h"
+#include "s3_kernels.h"
+
+struct s3_graph_s {
+    int device = 0;
+    s3_options opt{};
+    int64_t n = 0, m = 0, nnz = 0;
+    int32_t N = 0;
+    s3_format_info info{};
+
+    // size buckets (host copy of the layout) and per-bucket constants
+    std::vector<s3::HostBucket> buckets;
+    std::vector<double> K;        // per bucket
+    std::vector<float> Km;
+    std::vector<int32_t> Ke;
+    std::vector<float> target;
+
+    // device format
+    int32_t *d_ids = nullptr, *d_slot = nullptr;
+    int64_t *d_inc_ptr = nullptr;
+    int32_t *d_small = nullptr, *d_med = nullptr, *d_big_nodes = nullptr, *d_big_piece_ptr = nullptr;
+    int64_t *d_piece_start = nullptr;
+    int32_t *d_piece_len = nullptr;
+    int64_t n_small = 0, n_med = 0, n_big = 0, n_pieces = 0;
+
+    // scratch owned by the handle (reused by every call)
+    void *d_buf = nullptr;          // nnz values (8 bytes each) for the segmented reduce
+    void *d_partial = nullptr;      // n_pieces partial sums (8 bytes each)
+    float *d_comp = nullptr;        // n FP32 compensation terms (atomic mode)
+    unsigned long long *d_range = nullptr;
+    void *d_xh = nullptr, *d_yh = nullptr;   // n values each, staging for s3_sttsvc_host
+
+    // CCSS forest on the device (S3_LAYOUT_CCSS)
+    bool has_ccss = false;
+    struct CcssSeg { int32_t level, width; int64_t begin, end; };
+    struct CcssLeaf { int32_t s; int64_t begin, end; double K; float Km; int32_t Ke; };
+    std::vector<CcssSeg> ccss_segs;
+    std::vector<CcssLeaf> ccss_leaves;
+    std::vector<float> cc_level_target;  // per-level rescaling targets
+    int32_t *d_cc_vertex = nullptr, *d_cc_parent = nullptr, *d_cc_width = nullptr;
+    int64_t *d_cc_off = nullptr;
+    int32_t *d_leaf_node = nullptr, *d_leaf_vertex = nullptr, *d_leaf_slot = nullptr;
+    void *d_cc_values = nullptr;    // value_len coefficients (8 bytes each)
+    int64_t cc_value_len = 0;
+    int32_t *d_cc_scale = nullptr;  // global rescaling exponent of the last CCSS call
+
+    // NQZ scratch
+    double *d_nqz = nullptr;        // 4 n doubles: x, u, z (FP64), spare
+    float *d_x32 = nullptr, *d_z32 = nullptr;
+    double *d_red = nullptr;        // reduction partials
+    int32_t *d_flags = nullptr;     // [0] done, [1] phase-switch, ...
+    double *d_hist = nullptr;       // per-iteration (lmin, lmax)
+    int32_t hist_cap = 0;
+
+    int32_t last_launches = 0;       // kernels launched by the last S^3TTVc call
+    std::vector<void *> allocations;
+    int64_t device_bytes = 0;
+};
+
+namespace s3 {
+
+// Allocate count elements on the handle's device and remember the block.
+template <typename T>
+s3_status dev_alloc(s3_graph_s *g, T **p, size_t count) {
+    *p = nullptr;
+    if (count == 0) count = 1;
+    void *q = nullptr;
+    cudaError_t e = cudaMalloc(&q, count * sizeof(T));
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(S3_ENOMEM, std::string("cudaMalloc failed: ") + cudaGetErrorString(e));
+    }
+    g->allocations.push_back(q);
+    g->device_bytes += (int64_t)(count * sizeof(T));
+    *p = reinterpret_cast<T *>(q);
+    return S3_OK;
+}
+
+// RAII: make the handle's device current for the duration of a call.
+struct DeviceGuard {
+    int prev = -1;
+    bool changed = false;
+    explicit DeviceGuard(int dev) {
+        if (cudaGetDevice(&prev) == cudaSuccess && prev != dev) {
+            changed = cudaSetDevice(dev) == cudaSuccess;
+        }
+    }
+    ~DeviceGuard() {
+        if (changed) cudaSetDevice(prev);
+    }
+};
+
+s3_status cuda_fail(cudaError_t e, const char *what);
+s3_status prepare_device(int dev);
+// mid (optional) is recorded on st between the edge kernels and the reduce
+s3_status run_edges(s3_graph_s *g, s3_dtype dt, const void *x, void *y, int bias, const int32_t *skip,
+                    cudaStream_t st, cudaEvent_t mid = nullptr);
+s3_status run_ccss(s3_graph_s *g, s3_dtype dt, const void *x, void *y, int bias, const int32_t *skip,
+                   cudaStream_t st);
+s3_status upload_ccss(s3_graph_s *g, const HostFormat &f);
+
+}  // namespace s3
+
+#define S3_CUDA(expr)                                   \
+    do {                                                \
+        cudaError_t _e = (expr);                        \
+        if (_e != cudaSuccess) return s3::cuda_fail(_e, #expr); \
+    } while (0)

@@ -1,0 +1,70 @@
+// Host-callable launchers of the device kernels (internal to the library).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+namespace s3 {
+
+// One size bucket as the edge kernels see it.
+struct EdgeBucketArgs {
+    const int32_t *ids;   // member i of bucket edge k at ids[i * ld + k] (sorted members)
+    const int32_t *slot;  // same layout: node-sorted incidence slot (segmented reduce), or nullptr
+    int64_t m;            // edges in the bucket
+    int64_t ld;
+    int32_t s, N;         // edge size and rank
+    float target;         // rescaling target T(s,N)
+    double K;             // K(s,N) = s (N-1)! / (s! S(N,s))
+    float Km;             // K = Km * 2^Ke with Km in [0.5, 1)
+    int32_t Ke;
+};
+
+enum OutMode : int32_t {
+    kOutBuffer = 0,       // out[slot] = c
+    kOutAtomic = 1,       // out[v] += c (atomics)
+    kOutAtomicComp = 2    // FP32: out[v] += c with a two-sum compensation term in comp[v]
+};
+
+struct EdgeOutArgs {
+    void *out;                          // buffer (nnz) or y (n), element type of the call
+    float *comp;                        // FP32 compensation (n) for kOutAtomicComp
+    int32_t mode;                       // OutMode
+    int32_t bias;                       // 1: scale node v's results by 2^(-(N-1) e_v), x_v = m 2^e_v, m in [0.5,1)
+    unsigned long long *range_events;   // incremented for results that leave the normal range
+    const int32_t *skip;                // if non-null and *skip != 0 the kernel returns at once
+};
+
+// Launch the kernel for one bucket (s >= 1).  thread_max_w: windows up to this
+// use one thread per edge; block_threads: threads per block of that kernel.
+cudaError_t launch_edge_bucket_f32(const EdgeBucketArgs &b, const float *x, const EdgeOutArgs &o,
+                                   int thread_max_w, int block_threads, cudaStream_t st);
+cudaError_t launch_edge_bucket_f64(const EdgeBucketArgs &b, const double *x, const EdgeOutArgs &o,
+                                   int thread_max_w, int block_threads, cudaStream_t st);
+// One-time per-device set-up (shared-memory limits of the kernels).
+cudaError_t prepare_edge_kernels_f32();
+cudaError_t prepare_edge_kernels_f64();
+
+// Deterministic segmented reduce of a node-sorted buffer into y.
+struct ReduceArgs {
+    const int64_t *inc_ptr;        // n+1
+    const int32_t *small_nodes;    // degree <= kSmallDeg
+    int64_t n_small;
+    const int32_t *med_nodes;      // kSmallDeg < degree <= kPiece
+    int64_t n_med;
+    const int64_t *piece_start;    // pieces of big nodes
+    const int32_t *piece_len;
+    int64_t n_pieces;
+    const int32_t *big_nodes;
+    const int32_t *big_piece_ptr;  // n_big + 1
+    int64_t n_big;
+    void *partial;                 // n_pieces partial sums (float2 for FP32, double for FP64)
+    const int32_t *skip;
+};
+cudaError_t launch_reduce_f32(const ReduceArgs &r, const float *buf, float *y, cudaStream_t st);
+cudaError_t launch_reduce_f64(const ReduceArgs &r, const double *buf, double *y, cudaStream_t st);
+
+// y[v] += comp[v] (FP32 atomic mode), v < n
+cudaError_t launch_add_comp(float *y, const float *comp, int64_t n, const int32_t *skip, cudaStream_t st);
+
+}  // namespace s3

@@ -1,0 +1,503 @@
+// Per-edge truncated power-series kernels (the S^3TTVc hot path).
+//
+// For an edge e = (v_1 < ... < v_s) at rank N and a node v_i of e, the
+// contribution c(e, v_i) of Algorithm 2 is
+//     K(s,N) [t^(N-1)] E(x_{v_i}) prod_{j != i} Ebar(x_{v_j}),
+// E(x) = e^(x t), Ebar(x) = e^(x t) - 1 (Sec. II-A).  Because E = Ebar + 1,
+//     [t^(N-1)] E(x_{v_i}) F_{e,-i} = [t^(N-1)] F_e + [t^(N-1)] F_{e,-i},
+// with F_e = prod_j Ebar(x_{v_j}) and F_{e,-i} = Pre_i Suf_i, the product of
+// the factors before and after position i.  A product of k factors Ebar has
+// no term below t^k, so Pre_i only matters on degrees i-1 .. i-1+w-1 and
+// Suf_i on s-i .. s-i+w-1, with w = N-s+1: every series is kept as a window
+// of w coefficients.  Multiplying a window by Ebar(x) is a lower-triangular
+// Toeplitz product whose entries are a_k = x^k/k!, k >= 1.
+//
+// Per edge: prefix windows Pre_2..Pre_s forward (Pre_2 is the power table of
+// x_{v_1}), then suffix windows backward; each leave-one-out value is a dot of
+// Pre_i with the reversed Suf_i.  Before the products the edge's x values are
+// multiplied by an exact power of two g chosen from sum_u |x_u| (target
+// T(s,N), host side) so that all coefficients stay near 1; the result is
+// multiplied back by K(s,N) g^-(N-1) (exact exponent arithmetic).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cfloat>
+#include <cstdint>
+
+#include "s3_kernels.h"
+
+namespace s3 {
+
+// ------------------------------------------------------------ arithmetic --
+
+template <typename T> struct Arith;
+
+template <> struct Arith<float> {
+    // x = m 2^e with m in [0.5, 1) for normal x (0 -> 0, subnormal -> -126)
+    __device__ __forceinline__ static int expo(float v) {
+        int b = (__float_as_int(v) >> 23) & 0xff;
+        return b == 0 ? -126 : b - 126;
+    }
+    // exact 2^p for p in [-126, 127]
+    __device__ __forceinline__ static float pow2(int p) {
+        p = max(-126, min(127, p));
+        return __int_as_float((p + 127) << 23);
+    }
+    __device__ __forceinline__ static float absv(float v) { return fabsf(v); }
+    __device__ __forceinline__ static float tiny() { return FLT_MIN; }
+    __device__ __forceinline__ static float huge() { return FLT_MAX; }
+    __device__ __forceinline__ static float scale2(float v, int e) { return ldexpf(v, e); }
+    __device__ __forceinline__ static float fma_(float a, float b, float c) { return fmaf(a, b, c); }
+};
+
+template <> struct Arith<double> {
+    __device__ __forceinline__ static int expo(double v) {
+        int b = (int)((__double_as_longlong(v) >> 52) & 0x7ff);
+        return b == 0 ? -1022 : b - 1022;
+    }
+    __device__ __forceinline__ static double pow2(int p) {
+        p = max(-1022, min(1023, p));
+        return __longlong_as_double((long long)(p + 1023) << 52);
+    }
+    __device__ __forceinline__ static double absv(double v) { return fabs(v); }
+    __device__ __forceinline__ static double tiny() { return DBL_MIN; }
+    __device__ __forceinline__ static double huge() { return DBL_MAX; }
+    __device__ __forceinline__ static double scale2(double v, int e) { return ldexp(v, e); }
+    __device__ __forceinline__ static double fma_(double a, double b, double c) { return fma(a, b, c); }
+};
+
+// p such that 2^p * S is within a factor 2 of target (integer exponent arithmetic only).
+template <typename T>
+__device__ __forceinline__ int scale_exponent(T S, float target) {
+    if (!(S > T(0)) || !(S <= T(3.0e38))) return 0;
+    int es = Arith<T>::expo(S);
+    int et = Arith<float>::expo(target);
+    return et - es;
+}
+
+// ------------------------------------------------------ final scaling -----
+
+template <typename T>
+__device__ __forceinline__ T finalize_value(T val, const EdgeBucketArgs &b, int p, int bias_e,
+                                            unsigned long long *range_events);
+
+template <>
+__device__ __forceinline__ float finalize_value<float>(float val, const EdgeBucketArgs &b, int p, int bias_e,
+                                                       unsigned long long *range_events) {
+    int ex = b.Ke - p * (b.N - 1) - bias_e * (b.N - 1);
+    float c = ldexpf(val * b.Km, ex);
+    if (val > 0.f && !(c >= FLT_MIN && c <= FLT_MAX) && range_events) atomicAdd(range_events, 1ull);
+    return c;
+}
+
+template <>
+__device__ __forceinline__ double finalize_value<double>(double val, const EdgeBucketArgs &b, int p, int bias_e,
+                                                         unsigned long long *range_events) {
+    int ex = -p * (b.N - 1) - bias_e * (b.N - 1);
+    double c = ldexp(val * b.K, ex);
+    if (val > 0.0 && !(c >= DBL_MIN && c <= DBL_MAX) && range_events) atomicAdd(range_events, 1ull);
+    return c;
+}
+
+// -------------------------------------------------------------- scatter ---
+
+__device__ __forceinline__ void two_sum(float a, float b, float &s, float &err) {
+    s = a + b;
+    float bb = s - a;
+    err = (a - (s - bb)) + (b - bb);
+}
+
+// Add c to out[v] (atomic modes) with aggregation over the lanes of the warp
+// that target the same node.
+template <typename T>
+__device__ __forceinline__ void scatter_atomic(const EdgeOutArgs &o, int v, T c);
+
+template <>
+__device__ __forceinline__ void scatter_atomic<double>(const EdgeOutArgs &o, int v, double c) {
+    unsigned act = __activemask();
+    unsigned grp = __match_any_sync(act, v);
+    int lane = threadIdx.x & 31;
+    int leader = __ffs(grp) - 1;
+    double acc = 0.0;
+    for (unsigned mm = grp; mm; mm &= mm - 1) acc += __shfl_sync(grp, c, __ffs(mm) - 1);
+    if (lane == leader) atomicAdd(reinterpret_cast<double *>(o.out) + v, acc);
+}
+
+template <>
+__device__ __forceinline__ void scatter_atomic<float>(const EdgeOutArgs &o, int v, float c) {
+    unsigned act = __activemask();
+    unsigned grp = __match_any_sync(act, v);
+    int lane = threadIdx.x & 31;
+    int leader = __ffs(grp) - 1;
+    float acc = 0.f, cmp = 0.f;
+    for (unsigned mm = grp; mm; mm &= mm - 1) {
+        float t = __shfl_sync(grp, c, __ffs(mm) - 1);
+        float s, e;
+        two_sum(acc, t, s, e);
+        acc = s;
+        cmp += e;
+    }
+    if (lane == leader) {
+        float *y = reinterpret_cast<float *>(o.out);
+        float old = atomicAdd(y + v, acc);
+        if (o.mode == kOutAtomicComp) {
+            float s, e;
+            two_sum(old, acc, s, e);
+            e += cmp;
+            if (e != 0.f) atomicAdd(o.comp + v, e);
+        }
+    }
+}
+
+// ------------------------------------------------- thread-per-edge path ---
+
+// a[k] = x^(k+1)/(k+1)!, k = 0..W-1
+template <typename T, int W>
+__device__ __forceinline__ void power_table(T X, T (&a)[W]) {
+    a[0] = X;
+#pragma unroll
+    for (int k = 1; k < W; ++k) a[k] = a[k - 1] * (X * (T(1) / T(k + 1)));
+}
+
+// P <- P * Ebar(x) on the window (one degree up): P[j] = sum_{j' <= j} a[j-j'] P[j']
+template <typename T, int W>
+__device__ __forceinline__ void toeplitz_inplace(T (&P)[W], const T (&a)[W]) {
+#pragma unroll
+    for (int j = W - 1; j >= 0; --j) {
+        T acc = a[j] * P[0];
+#pragma unroll
+        for (int jp = 1; jp <= j; ++jp) acc = Arith<T>::fma_(a[j - jp], P[jp], acc);
+        P[j] = acc;
+    }
+}
+
+template <typename T>
+__device__ __forceinline__ void emit_thread(const EdgeBucketArgs &b, const EdgeOutArgs &o, int64_t e, int q,
+                                            T val, int p, T xhat) {
+    int bias_e = o.bias ? (Arith<T>::expo(xhat) - p) : 0;
+    T c = finalize_value<T>(val, b, p, bias_e, o.range_events);
+    if (o.mode == kOutBuffer) {
+        int sl = __ldg(b.slot + (int64_t)q * b.ld + e);
+        reinterpret_cast<T *>(o.out)[sl] = c;
+    } else {
+        int v = __ldg(b.ids + (int64_t)q * b.ld + e);
+        scatter_atomic<T>(o, v, c);
+    }
+}
+
+// Shared memory per thread: s values (scaled x) + (s-2) windows of W (Pre_2..Pre_{s-1}),
+// interleaved across the block (element k of thread t at k * blockDim + t).
+template <typename T, int W>
+__global__ void __launch_bounds__(256) edge_thread_kernel(EdgeBucketArgs b, const T *__restrict__ x,
+                                                          EdgeOutArgs o) {
+    if (o.skip && *o.skip) return;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T *sm = reinterpret_cast<T *>(smem_raw);
+    const int BS = blockDim.x;
+    const int tid = threadIdx.x;
+    const int64_t e = (int64_t)blockIdx.x * BS + tid;
+    if (e >= b.m) return;
+    const int s = b.s;
+    T *Xs = sm + tid;
+    T *Pre = sm + (int64_t)s * BS + tid;
+
+    T S = T(0);
+    for (int i = 0; i < s; ++i) {
+        int v = __ldg(b.ids + (int64_t)i * b.ld + e);
+        T X = __ldg(x + v);
+        Xs[i * BS] = X;
+        S += Arith<T>::absv(X);
+    }
+    const int p = scale_exponent<T>(S, b.target);
+    const T g = Arith<T>::pow2(p);
+    for (int i = 0; i < s; ++i) Xs[i * BS] *= g;
+
+    // forward: P = Pre_2, then Pre_3 .. Pre_s (windows Pre_2..Pre_{s-1} kept in shared memory)
+    T P[W];
+    power_table<T, W>(Xs[0], P);
+    for (int i = 1; i <= s - 2; ++i) {
+#pragma unroll
+        for (int j = 0; j < W; ++j) Pre[((i - 1) * W + j) * BS] = P[j];
+        T a[W];
+        power_table<T, W>(Xs[i * BS], a);
+        toeplitz_inplace<T, W>(P, a);
+    }
+    // P = Pre_s.  backward: Q = Suf_{s-1} = Ebar(x_{v_s})
+    T Q[W];
+    power_table<T, W>(Xs[(s - 1) * BS], Q);
+    T F = T(0);
+#pragma unroll
+    for (int j = 0; j <= W - 2; ++j) F = Arith<T>::fma_(P[j], Q[W - 2 - j], F);
+    emit_thread<T>(b, o, e, s - 1, F + P[W - 1], p, Xs[(s - 1) * BS]);
+    T top = T(0);
+    for (int q = s - 2; q >= 1; --q) {
+        // Q = Suf_{q+1}; Pre_{q+1} sits in slot q-1
+        T D = T(0);
+#pragma unroll
+        for (int j = 0; j < W; ++j) D = Arith<T>::fma_(Pre[((q - 1) * W + j) * BS], Q[W - 1 - j], D);
+        emit_thread<T>(b, o, e, q, F + D, p, Xs[q * BS]);
+        T a[W];
+        power_table<T, W>(Xs[q * BS], a);
+        if (q >= 2) {
+            toeplitz_inplace<T, W>(Q, a);
+        } else {
+#pragma unroll
+            for (int jp = 0; jp < W; ++jp) top = Arith<T>::fma_(a[W - 1 - jp], Q[jp], top);
+        }
+    }
+    T D1 = (s == 2) ? Q[W - 1] : top;
+    emit_thread<T>(b, o, e, 0, F + D1, p, Xs[0]);
+}
+
+// Size-1 edges: c(e, v) = x_v^(N-1) (K(1,N) [t^(N-1)] e^(x t) with K(1,N) = (N-1)!).
+template <typename T>
+__global__ void edge_single_kernel(EdgeBucketArgs b, const T *__restrict__ x, EdgeOutArgs o) {
+    if (o.skip && *o.skip) return;
+    int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= b.m) return;
+    int v = __ldg(b.ids + e);
+    T X = __ldg(x + v);
+    // X = m 2^ex, m in [0.5,1): X^(N-1) = m^(N-1) 2^((N-1) ex)
+    int ex = Arith<T>::expo(X);
+    T mm = X * Arith<T>::pow2(-ex);
+    T r = T(1), base = mm;
+    for (int k = b.N - 1; k > 0; k >>= 1) {
+        if (k & 1) r *= base;
+        base *= base;
+    }
+    int bias_e = o.bias ? ex : 0;
+    T c = Arith<T>::scale2(r, (b.N - 1) * (ex - bias_e));
+    if (r != T(0) && !(Arith<T>::absv(c) >= Arith<T>::tiny() && Arith<T>::absv(c) <= Arith<T>::huge()) &&
+        o.range_events)
+        atomicAdd(o.range_events, 1ull);
+    if (o.mode == kOutBuffer) {
+        reinterpret_cast<T *>(o.out)[__ldg(b.slot + e)] = c;
+    } else {
+        scatter_atomic<T>(o, v, c);
+    }
+}
+
+// --------------------------------------------------- warp-per-edge path ---
+
+template <typename T>
+__device__ __forceinline__ T warp_sum(T v) {
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) v += __shfl_xor_sync(0xffffffffu, v, d);
+    return v;
+}
+
+// out[k] = x^(k+1)/(k+1)!, k < W, as a prefix product of x/(k+1) over the lanes.
+template <typename T>
+__device__ __forceinline__ void power_table_warp(T X, T *out, int W) {
+    const int lane = threadIdx.x & 31;
+    T carry = T(1);
+    for (int base = 0; base < W; base += 32) {
+        int k = base + lane;
+        T c = k < W ? X / T(k + 1) : T(1);
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            T t = __shfl_up_sync(0xffffffffu, c, d);
+            if (lane >= d) c *= t;
+        }
+        c *= carry;
+        if (k < W) out[k] = c;
+        carry = __shfl_sync(0xffffffffu, c, 31);
+    }
+}
+
+// Per warp shared memory (elements of T): Xs[s] | C[s] | Pre[(s-2) W] (Pre_2..Pre_{s-1}) |
+// Pcur[W] | Q[W] | A[W] | R[W].  One edge per warp, grid-stride over the bucket.
+template <typename T>
+__global__ void __launch_bounds__(128) edge_warp_kernel(EdgeBucketArgs b, const T *__restrict__ x, EdgeOutArgs o,
+                                                        int W, int64_t per_warp) {
+    if (o.skip && *o.skip) return;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int lane = threadIdx.x & 31;
+    const int wib = threadIdx.x >> 5;
+    const int wpb = blockDim.x >> 5;
+    T *base = reinterpret_cast<T *>(smem_raw) + (int64_t)wib * per_warp;
+    const int s = b.s;
+    T *Xs = base;
+    T *C = Xs + s;
+    T *Pre = C + s;
+    T *Pc = Pre + (int64_t)(s > 2 ? s - 2 : 0) * W;
+    T *Q = Pc + W;
+    T *A = Q + W;
+    T *R = A + W;
+    for (int64_t e = (int64_t)blockIdx.x * wpb + wib; e < b.m; e += (int64_t)gridDim.x * wpb) {
+        T part = T(0);
+        for (int i = lane; i < s; i += 32) {
+            T X = __ldg(x + __ldg(b.ids + (int64_t)i * b.ld + e));
+            Xs[i] = X;
+            part += Arith<T>::absv(X);
+        }
+        T S = warp_sum(part);
+        const int p = scale_exponent<T>(S, b.target);
+        const T g = Arith<T>::pow2(p);
+        __syncwarp();
+        for (int i = lane; i < s; i += 32) Xs[i] *= g;
+        __syncwarp();
+        // forward
+        power_table_warp<T>(Xs[0], Pc, W);
+        __syncwarp();
+        for (int i = 1; i <= s - 2; ++i) {
+            T *slotp = Pre + (int64_t)(i - 1) * W;
+            for (int j = lane; j < W; j += 32) slotp[j] = Pc[j];
+            power_table_warp<T>(Xs[i], A, W);
+            __syncwarp();
+            for (int j = lane; j < W; j += 32) {
+                T acc = T(0);
+                for (int jp = 0; jp <= j; ++jp) acc = Arith<T>::fma_(A[j - jp], slotp[jp], acc);
+                Pc[j] = acc;
+            }
+            __syncwarp();
+        }
+        // backward
+        power_table_warp<T>(Xs[s - 1], Q, W);
+        __syncwarp();
+        T fp = T(0);
+        for (int j = lane; j <= W - 2; j += 32) fp = Arith<T>::fma_(Pc[j], Q[W - 2 - j], fp);
+        const T F = warp_sum(fp);
+        if (lane == 0) C[s - 1] = F + Pc[W - 1];
+        T top = T(0);
+        for (int q = s - 2; q >= 1; --q) {
+            const T *pre = Pre + (int64_t)(q - 1) * W;
+            T dp = T(0);
+            for (int j = lane; j < W; j += 32) dp = Arith<T>::fma_(pre[j], Q[W - 1 - j], dp);
+            T D = warp_sum(dp);
+            if (lane == 0) C[q] = F + D;
+            power_table_warp<T>(Xs[q], A, W);
+            __syncwarp();
+            if (q >= 2) {
+                for (int j = lane; j < W; j += 32) {
+                    T acc = T(0);
+                    for (int jp = 0; jp <= j; ++jp) acc = Arith<T>::fma_(A[j - jp], Q[jp], acc);
+                    R[j] = acc;
+                }
+                __syncwarp();
+                T *t = Q;
+                Q = R;
+                R = t;
+            } else {
+                T tp = T(0);
+                for (int jp = lane; jp < W; jp += 32) tp = Arith<T>::fma_(A[W - 1 - jp], Q[jp], tp);
+                top = warp_sum(tp);
+            }
+        }
+        if (lane == 0) C[0] = F + (s == 2 ? Q[W - 1] : top);
+        __syncwarp();
+        for (int q = lane; q < s; q += 32) {
+            int bias_e = o.bias ? (Arith<T>::expo(Xs[q]) - p) : 0;
+            T c = finalize_value<T>(C[q], b, p, bias_e, o.range_events);
+            if (o.mode == kOutBuffer) {
+                reinterpret_cast<T *>(o.out)[__ldg(b.slot + (int64_t)q * b.ld + e)] = c;
+            } else {
+                int v = __ldg(b.ids + (int64_t)q * b.ld + e);
+                if constexpr (sizeof(T) == 8) {
+                    atomicAdd(reinterpret_cast<double *>(o.out) + v, (double)c);
+                } else {
+                    float *y = reinterpret_cast<float *>(o.out);
+                    float old = atomicAdd(y + v, (float)c);
+                    if (o.mode == kOutAtomicComp) {
+                        float sm, er;
+                        two_sum(old, (float)c, sm, er);
+                        if (er != 0.f) atomicAdd(o.comp + v, er);
+                    }
+                }
+            }
+        }
+        __syncwarp();
+        // Q/R may have been swapped; restore the fixed layout for the next edge
+        Q = Pc + W;
+        R = A + W;
+    }
+}
+
+}  // namespace s3
+
+// ------------------------------------------------------------- launchers --
+
+namespace s3 {
+
+constexpr size_t kSmemCap = 96 * 1024;        // per block, thread-per-edge kernel
+constexpr size_t kSmemCapWarp = 200 * 1024;   // per block, warp-per-edge kernel
+constexpr int kMaxThreadW = 32;
+
+template <typename T, int W>
+cudaError_t launch_thread_w(const EdgeBucketArgs &b, const T *x, const EdgeOutArgs &o, int bs, cudaStream_t st) {
+    size_t per_thread = (size_t)(b.s + (b.s > 2 ? (b.s - 2) * W : 0)) * sizeof(T);
+    size_t smem = per_thread * (size_t)bs;
+    int64_t grid = (b.m + bs - 1) / bs;
+    edge_thread_kernel<T, W><<<(unsigned)grid, bs, smem, st>>>(b, x, o);
+    return cudaGetLastError();
+}
+
+template <typename T, int W>
+cudaError_t prepare_thread_w() {
+    return cudaFuncSetAttribute(edge_thread_kernel<T, W>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemCap);
+}
+
+#define S3_W_CASES(M) \
+    M(1) M(2) M(3) M(4) M(5) M(6) M(7) M(8) M(9) M(10) M(11) M(12) M(13) M(14) M(15) M(16) \
+    M(17) M(18) M(19) M(20) M(21) M(22) M(23) M(24) M(25) M(26) M(27) M(28) M(29) M(30) M(31) M(32)
+
+template <typename T>
+cudaError_t prepare_edge_kernels_t() {
+    cudaError_t err = cudaSuccess;
+#define S3_PREP(w) if (err == cudaSuccess) err = prepare_thread_w<T, w>();
+    S3_W_CASES(S3_PREP)
+#undef S3_PREP
+    if (err == cudaSuccess)
+        err = cudaFuncSetAttribute(edge_warp_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemCapWarp);
+    return err;
+}
+
+// Threads per block for the thread-per-edge kernel so that the block's shared
+// memory stays under kSmemCap; 0 if not even one warp fits.
+template <typename T>
+int thread_block_size(int s, int W, int want) {
+    size_t per_thread = (size_t)(s + (s > 2 ? (s - 2) * W : 0)) * sizeof(T);
+    int bs = want;
+    while (bs > 32 && per_thread * (size_t)bs > kSmemCap) bs -= 32;
+    return per_thread * (size_t)bs > kSmemCap ? 0 : bs;
+}
+
+template <typename T>
+cudaError_t launch_edge_bucket_t(const EdgeBucketArgs &b, const T *x, const EdgeOutArgs &o, int thread_max_w,
+                                 int block_threads, cudaStream_t st) {
+    if (b.m <= 0) return cudaSuccess;
+    if (b.s == 1) {
+        int bs = 256;
+        edge_single_kernel<T><<<(unsigned)((b.m + bs - 1) / bs), bs, 0, st>>>(b, x, o);
+        return cudaGetLastError();
+    }
+    const int W = b.N - b.s + 1;
+    if (thread_max_w <= 0 || thread_max_w > kMaxThreadW) thread_max_w = kMaxThreadW;
+    if (block_threads <= 0) block_threads = 128;
+    if (W <= thread_max_w) {
+        int bs = thread_block_size<T>(b.s, W, block_threads);
+        if (bs > 0) {
+            switch (W) {
+#define S3_CASE(w) \
+    case w: return launch_thread_w<T, w>(b, x, o, bs, st);
+                S3_W_CASES(S3_CASE)
+#undef S3_CASE
+                default: break;
+            }
+        }
+    }
+    // one warp per edge
+    int64_t per_warp = 2 * (int64_t)b.s + (int64_t)(b.s > 2 ? b.s - 2 : 0) * W + 4 * (int64_t)W;
+    per_warp = (per_warp + 3) / 4 * 4;
+    int wpb = 4;
+    while (wpb > 1 && (size_t)wpb * per_warp * sizeof(T) > kSmemCapWarp) wpb /= 2;
+    size_t smem = (size_t)wpb * per_warp * sizeof(T);
+    if (smem > kSmemCapWarp) return cudaErrorInvalidConfiguration;
+    int64_t grid = (b.m + wpb - 1) / wpb;
+    if (grid > (1 << 22)) grid = 1 << 22;
+    edge_warp_kernel<T><<<(unsigned)grid, wpb * 32, smem, st>>>(b, x, o, W, per_warp);
+    return cudaGetLastError();
+}
+
+}  // namespace s3

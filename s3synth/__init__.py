@@ -98,18 +98,31 @@ def geometric_sizes(m, prob, lo, hi, rng):
 # --------------------------------------------------------------- members ---
 
 def _fix_repeats(edge_of, draw, resample, rng, max_rounds=1000):
-    """Redraw members that repeat inside their edge until none do."""
+    """Redraw members that repeat inside their edge until none do.
+
+    Every later occurrence of a node inside an edge is redrawn (in position
+    order); after the first pass only the edges that had a repeat are checked
+    again.  ``edge_of`` is non-decreasing (edges are contiguous)."""
+    span = int(draw.max()) + 1 if draw.size else 1
+    m = int(edge_of[-1]) + 1 if edge_of.size else 0
+    ptr = np.zeros(m + 1, dtype=np.int64)
+    np.cumsum(np.bincount(edge_of, minlength=m), out=ptr[1:])
+    idx = np.arange(draw.size, dtype=np.int64)
     for _ in range(max_rounds):
-        order = np.lexsort((draw, edge_of))
-        e_sorted = edge_of[order]
-        d_sorted = draw[order]
-        dup = np.zeros(draw.size, dtype=bool)
-        same = (e_sorted[1:] == e_sorted[:-1]) & (d_sorted[1:] == d_sorted[:-1])
-        dup[order[1:][same]] = True
-        k = int(dup.sum())
-        if k == 0:
+        key = edge_of[idx] * span + draw[idx]
+        order = np.argsort(key, kind="stable")
+        ks = key[order]
+        same = ks[1:] == ks[:-1]
+        if not same.any():
             return draw
-        draw[dup] = resample(k)
+        dup = np.sort(idx[order[1:][same]])
+        new = resample(dup.size)
+        span = max(span, int(new.max()) + 1)
+        draw[dup] = new
+        bad = np.unique(edge_of[dup])
+        lens = ptr[bad + 1] - ptr[bad]
+        starts = np.repeat(ptr[bad] - np.concatenate(([0], np.cumsum(lens)[:-1])), lens)
+        idx = starts + np.arange(int(lens.sum()), dtype=np.int64)
     raise RuntimeError("could not draw members without repeats")
 
 

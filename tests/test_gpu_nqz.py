@@ -1,0 +1,73 @@
+"""GPU NQZ (Algorithm 1) against the FP64 CPU oracle."""
+import numpy as np
+import pytest
+
+import oracle
+import s3synth
+from oracle.nqz import nqz
+from test_oracle_nqz import regular_hypergraph
+
+pytestmark = pytest.mark.gpu
+
+
+def _run(hg, **kw):
+    import paper_2311_08595_gb300 as s3
+    g = s3.s3_build_format(hg.n, hg.edge_ptr, hg.members)
+    x, res = s3.s3_hcentrality(g, **kw)
+    return x.cpu().numpy(), res
+
+
+@pytest.fixture(scope="module")
+def medium():
+    hg, _ = s3synth.largest_component(s3synth.config_powerlaw(n=20000, m=100000, rank=25, seed=7))
+    ref = nqz(hg, tol=1e-8, nthreads=oracle.max_threads())
+    return hg, ref
+
+
+def test_fp64_matches_oracle(medium):
+    hg, ref = medium
+    x, res = _run(hg, tol=1e-8, precision=0)
+    assert res["converged"]
+    assert abs(res["iters"] - ref.iters) <= 1
+    assert np.max(np.abs(x - ref.x) / ref.x) < 1e-10
+    lam = 0.5 * (res["lambda_min"] + res["lambda_max"])
+    assert abs(lam - ref.lam) < 1e-8 * ref.lam
+
+
+def test_fp32_mixed_reaches_same_vector(medium):
+    hg, ref = medium
+    x, res = _run(hg, tol=1e-8, precision=1)
+    assert res["converged"] and res["iters_fp32"] > 0
+    assert np.max(np.abs(x - ref.x) / ref.x) < 1e-7
+    print(f"mixed: {res['iters']} iterations ({res['iters_fp32']} FP32), oracle {ref.iters}")
+
+
+def test_regular_hypergraph_one_iteration():
+    hg = regular_hypergraph(300, 4, 2, 7, 2)
+    x, res = _run(hg, tol=1e-12)
+    assert res["converged"] and res["iters"] == 1
+    assert np.allclose(x, 1.0 / hg.n, rtol=1e-13)
+    assert abs(res["lambda_max"] - 4.0) < 1e-12
+
+
+def test_warm_start_same_limit(medium):
+    import torch
+    hg, ref = medium
+    x0 = torch.tensor(s3synth.x_uniform(hg.n, 0.5, 2.0, 3), dtype=torch.float64, device="cuda")
+    x, res = _run(hg, tol=1e-8, x0=x0)
+    assert res["converged"] and np.max(np.abs(x - ref.x) / ref.x) < 1e-7
+
+
+def test_isolated_node_rejected():
+    import paper_2311_08595_gb300 as s3
+    hg = s3synth.from_edges(4, [(0, 1), (1, 2)])
+    g = s3.s3_build_format(hg.n, hg.edge_ptr, hg.members)
+    with pytest.raises(s3.S3Error) as ei:
+        s3.s3_hcentrality(g)
+    assert ei.value.status == 1
+
+
+def test_iteration_cap_reports_noconv(medium):
+    hg, _ = medium
+    x, res = _run(hg, tol=1e-14, max_iter=5, raise_on_noconv=False)
+    assert res["status"] == "S3_ENOCONV" and res["iters"] == 5 and not res["converged"]

@@ -1,0 +1,190 @@
+"""GPU S^3TTVc vs the FP64 CPU oracle, element by element, through the C ABI.
+
+Tolerances (per node, relative): FP64 path 1e-12, FP32 path 1e-5 for ranks up
+to 25 (the bound stated for the method); rank-100 FP32 results are checked
+against a looser 1e-4 bound and their error is printed.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import s3synth
+from gpu_util import gpu_sttsvc, rel_err
+
+pytestmark = pytest.mark.gpu
+
+F64_TOL = 1e-12
+F32_TOL = 1e-5
+
+
+def check(hg, x, N=None, layouts=(None,), reduces=(0, 1), f32_tol=F32_TOL, f64_tol=F64_TOL, **opts):
+    want = oracle.ttsv1(hg, x, N=N)
+    errs = {}
+    for layout in layouts:
+        for red in reduces:
+            for dt, tol in (("f64", f64_tol), ("f32", f32_tol)):
+                y = gpu_sttsvc(hg, x, dt, layout=layout, rank=N, reduce=red, **opts)
+                e = rel_err(y, want)
+                errs[(layout, red, dt)] = e
+                assert e <= tol, f"{hg.name} layout={layout} reduce={red} {dt}: {e:.3e} > {tol}"
+    return errs
+
+
+@pytest.mark.parametrize("seed,N", [(0, 4), (1, 4), (2, 5), (3, 6), (4, 4), (5, 7)])
+def test_tiny_cases(seed, N):
+    hg = s3synth.tiny_case(seed=seed, rank=4)
+    check(hg, s3synth.x_uniform(hg.n, 0.05, 1.5, seed), N=N, layouts=(None, "ccss"))
+
+
+def test_fig1_example():
+    hg = s3synth.fig1_example()
+    check(hg, s3synth.x_uniform(hg.n, 0.0, 1.0, 3), layouts=(None, "ccss"))
+
+
+def test_small_config_all_paths():
+    # n=1000, m=5000, sizes U{2..5}, x ~ U(0,1)
+    hg = s3synth.config_small(seed=1)
+    x = s3synth.x_uniform(hg.n, 0.0, 1.0, 1)
+    check(hg, x, layouts=(None, "ccss"))
+    # every window through the warp-per-edge kernel, and small thread blocks
+    check(hg, x, reduces=(0,), thread_max_w=1)
+    check(hg, x, reduces=(0,), block_threads=32)
+
+
+def test_powerlaw_medium_rank25():
+    hg = s3synth.config_powerlaw(n=20000, m=100000, rank=25, seed=11)
+    x = s3synth.x_uniform(hg.n, 0.5, 1.5, 11)
+    check(hg, x, layouts=(None, "ccss"))
+    check(hg, x, reduces=(0,), thread_max_w=8)
+
+
+def test_large_rank_100():
+    hg = s3synth.config_large_rank(n=3000, m=4000, rank=100, seed=12)
+    x = s3synth.x_uniform(hg.n, 0.5, 1.5, 12)
+    errs = check(hg, x, reduces=(0, 1), f32_tol=1e-4, f64_tol=1e-11, layouts=(None, "ccss"))
+    print("rank-100 errors:", {k: f"{v:.2e}" for k, v in errs.items()})
+
+
+def test_edge_cases_sizes_rank_isolated_duplicates():
+    edges = [(0,), (1, 2), (1, 2), (0, 3, 4), (5,), (2, 6, 7, 8, 9), (3, 4)]
+    hg = s3synth.from_edges(12, edges)          # nodes 10, 11 isolated; one duplicate edge
+    x = s3synth.x_uniform(hg.n, 0.2, 1.2, 5)
+    x[6] = 0.0                                  # a zero entry
+    for N in (5, 6, 9, 30):
+        check(hg, x, N=N, layouts=(None, "ccss"))
+    y = gpu_sttsvc(hg, x, "f64", rank=6)
+    assert y[10] == 0.0 and y[11] == 0.0
+
+
+def test_no_edges_gives_zero():
+    hg = s3synth.Hypergraph(7, np.zeros(1, dtype=np.int64), np.zeros(0, dtype=np.int32), rank=3)
+    for dt in ("f32", "f64"):
+        assert np.all(gpu_sttsvc(hg, np.ones(7), dt, rank=3) == 0.0)
+
+
+def test_maximum_rank_edges():
+    # S3_MAX_RANK = 128: one edge of every width class at rank 128
+    rng = np.random.default_rng(0)
+    edges = [tuple(rng.choice(300, size=s, replace=False)) for s in (2, 3, 17, 64, 100, 127, 128)]
+    hg = s3synth.from_edges(300, edges)
+    x = s3synth.x_uniform(hg.n, 0.7, 1.3, 1)
+    check(hg, x, N=128, f32_tol=2e-4, f64_tol=1e-11, reduces=(0,), layouts=(None, "ccss"))
+
+
+def test_ones_give_degrees():
+    hg = s3synth.config_powerlaw(n=5000, m=20000, rank=12, seed=3)
+    d = hg.degrees().astype(np.float64)
+    for dt, tol in (("f64", 1e-13), ("f32", 2e-6)):
+        y = gpu_sttsvc(hg, np.ones(hg.n), dt)
+        assert rel_err(y[d > 0], d[d > 0]) < tol
+
+
+def test_segmented_reduce_is_deterministic():
+    import torch
+
+    import paper_2311_08595_gb300 as s3
+    hg = s3synth.config_powerlaw(n=20000, m=100000, rank=25, seed=5)
+    g = s3.s3_build_format(hg.n, hg.edge_ptr, hg.members)
+    for dt in (torch.float32, torch.float64):
+        x = torch.tensor(s3synth.x_uniform(hg.n, 0.5, 1.5, 5), dtype=dt, device="cuda")
+        ys = []
+        for _ in range(3):
+            y = torch.empty_like(x)
+            s3.s3_sttsvc(g, x, y)
+            ys.append(y.cpu())
+        assert all(torch.equal(ys[0], t) for t in ys[1:])
+
+
+def test_host_entry_point_matches_device():
+    import torch
+
+    import paper_2311_08595_gb300 as s3
+    hg = s3synth.config_small(seed=2)
+    g = s3.s3_build_format(hg.n, hg.edge_ptr, hg.members)
+    x = s3synth.x_uniform(hg.n, 0, 1, 2)
+    for dt in (torch.float32, torch.float64):
+        xh = torch.tensor(x, dtype=dt).pin_memory()
+        yh = torch.empty_like(xh).pin_memory()
+        s3.s3_sttsvc_host(g, xh, yh)
+        yd = torch.empty(hg.n, dtype=dt, device="cuda")
+        s3.s3_sttsvc(g, xh.cuda(), yd)
+        torch.cuda.synchronize()
+        assert torch.equal(yh, yd.cpu())
+
+
+def test_range_events_counted():
+    import torch
+
+    import paper_2311_08595_gb300 as s3
+    hg = s3synth.config_small(seed=3)
+    g = s3.s3_build_format(hg.n, hg.edge_ptr, hg.members)
+    s3.s3_range_events(g, reset=True)
+    y = torch.empty(hg.n, dtype=torch.float32, device="cuda")
+    s3.s3_sttsvc(g, torch.full((hg.n,), 0.5, device="cuda"), y)
+    assert s3.s3_range_events(g) == 0
+    s3.s3_sttsvc(g, torch.full((hg.n,), 1e-12, device="cuda"), y)   # (1e-12)^4 underflows FP32
+    assert s3.s3_range_events(g, reset=True) > 0
+    y64 = torch.empty(hg.n, dtype=torch.float64, device="cuda")
+    s3.s3_sttsvc(g, torch.full((hg.n,), 1e-12, dtype=torch.float64, device="cuda"), y64)
+    assert s3.s3_range_events(g) == 0
+
+
+def test_invalid_calls_raise():
+    import torch
+
+    import paper_2311_08595_gb300 as s3
+    hg = s3synth.config_small(seed=1)
+    g = s3.s3_build_format(hg.n, hg.edge_ptr, hg.members)
+    x = torch.ones(hg.n, device="cuda")
+    with pytest.raises(s3.S3Error):
+        s3.s3_sttsvc_layout(g, s3.S3_LAYOUT_CCSS, x, torch.empty_like(x))   # built without the forest
+    with pytest.raises(ValueError):
+        s3.s3_sttsvc(g, x[:10], torch.empty_like(x))
+
+
+@pytest.mark.parametrize("dt,tol", [("f64", F64_TOL), ("f32", F32_TOL)])
+def test_full_size_powerlaw_sampled(dt, tol):
+    # n=1M, m=5M, Zipf(2.5) sizes on {2..25}, Chung-Lu gamma=2.1: the benchmark's
+    # workload and launch configuration; sampled nodes (including the hubs) vs the oracle
+    hg = _big()
+    x = s3synth.x_uniform(hg.n, 0.5, 1.5, 21)
+    y = gpu_sttsvc(hg, x, dt)
+    deg = hg.degrees()
+    rng = np.random.default_rng(0)
+    nodes = np.unique(np.concatenate([np.argsort(deg)[-8:], rng.integers(0, hg.n, 120)]))
+    want = oracle.ttsv1(hg, x, nodes=nodes, nthreads=oracle.max_threads())
+    e = rel_err(y[nodes], want)
+    assert e <= tol, f"{dt}: {e:.3e}"
+    # B 1 = d holds at any size
+    y1 = gpu_sttsvc(hg, np.ones(hg.n), dt)
+    assert rel_err(y1[deg > 0], deg[deg > 0]) <= (1e-13 if dt == "f64" else 2e-6)
+
+
+_BIG = None
+
+
+def _big():
+    global _BIG
+    if _BIG is None:
+        _BIG = s3synth.config_powerlaw()
+    return _BIG
