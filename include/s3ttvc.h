@@ -221,6 +221,41 @@ s3_status s3_nqz_options_init(s3_nqz_options *opt);
 s3_status s3_hcentrality(s3_graph_t g, const s3_nqz_options *opt, const double *x0, double *x_out,
                          s3_nqz_result *res, void *stream);
 
+/* ----------------------------------------------- allocation-free call --- */
+
+/* Largest node count s3_sttsvc_f32_noalloc accepts (its fixed scratch: 4 bytes per node). */
+#define S3_NOALLOC_MAX_NODES (1 << 22)
+
+/*
+ * FP32 y = B x^(N-1) for callers that cannot allocate device memory: code
+ * being captured into a CUDA graph (allocation is illegal during capture),
+ * pipelines that fix all their memory up front, or hosts whose own allocator
+ * owns the device.  Such callers can neither build a graph handle nor pass a
+ * workspace, so this entry point takes the hypergraph as plain device arrays
+ * and allocates nothing: its only scratch (one FP32 two-sum compensation term
+ * per node) is a fixed array of S3_NOALLOC_MAX_NODES floats (16 MiB) compiled
+ * into the library, which every GPU that loads the library holds until the
+ * process exits.  The paper has no counterpart of this entry point.
+ *
+ * n: nodes, 1 <= n <= S3_NOALLOC_MAX_NODES (S3_EINVAL otherwise).
+ * m: edges.  rank: N, 1..S3_MAX_RANK.
+ * edge_ptr: device, m+1 int64 CSR offsets.  members: device, int32 node ids
+ *   (any order inside an edge, no repeats).  Edges whose size is outside
+ *   1..rank or that hold an id outside [0, n) are skipped, not reported.
+ * x: device, n floats.  y: device, n floats, overwritten (must not overlap x).
+ * stream: cudaStream_t as void*; the call only enqueues work.
+ * Contributions are added with atomics (summation order varies run to run)
+ * and each addition's rounding error is kept in the scratch array and folded
+ * into y at the end; the call zeroes y and the scratch itself.
+ * The first call on a device resolves the scratch array's device address
+ * (cudaGetSymbolAddress) and sets a kernel attribute, so make that first call
+ * before any stream capture.  Every call on a device shares the one scratch
+ * array: calls whose work overlaps on the GPU (different streams, or several
+ * host threads) race and give wrong results -- order them.
+ */
+s3_status s3_sttsvc_f32_noalloc(int64_t n, int64_t m, int32_t rank, const int64_t *edge_ptr,
+                                const int32_t *members, const float *x, float *y, void *stream);
+
 /* ------------------------------------------------------------- cleanup --- */
 
 /* Release the handle and its device memory (synchronises its device).  NULL is allowed. */

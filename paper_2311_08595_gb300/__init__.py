@@ -26,7 +26,7 @@ from ._lib import (S3_F32, S3_F64, S3_LAYOUT_CCSS, S3_LAYOUT_EDGE, S3_REDUCE_ATO
 __all__ = [
     "Graph", "S3Error", "s3_options_init", "s3_format_inspect", "s3_build_format", "s3_graph_query",
     "s3_sttsvc", "s3_sttsvc_layout", "s3_sttsvc_host", "s3_sttsvc_profile", "s3_range_events", "s3_hcentrality",
-    "s3_nqz_options_init", "s3_destroy", "s3_version", "lib_path",
+    "s3_nqz_options_init", "s3_sttsvc_f32_noalloc", "s3_destroy", "s3_version", "lib_path",
 ]
 
 
@@ -199,6 +199,19 @@ def s3_hcentrality(g, x0=None, x_out=None, stream=None, raise_on_noconv=True, **
     if st != _lib.S3_OK and not (st == _lib.S3_ENOCONV and not raise_on_noconv):
         check(st)
     return x_out, out
+
+
+def s3_sttsvc_f32_noalloc(n, edge_ptr, members, x, y, rank, stream=None):
+    """FP32 S^3TTVc that allocates no device memory (see include/s3ttvc.h).
+
+    edge_ptr (int64, m+1), members (int32), x and y (float32, n) are CUDA tensors
+    the caller already owns; the library uses only its fixed built-in scratch."""
+    for t, nm in ((edge_ptr, "edge_ptr"), (members, "members"), (x, "x"), (y, "y")):
+        if not t.is_cuda or not t.is_contiguous():
+            raise ValueError(f"{nm} must be a contiguous CUDA tensor")
+    check(load().s3_sttsvc_f32_noalloc(int(n), edge_ptr.numel() - 1, int(rank), ptr(edge_ptr), ptr(members),
+                                       ptr(x), ptr(y), _stream(stream)))
+    return y
 
 
 def s3_destroy(g):

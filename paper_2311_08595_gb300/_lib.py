@@ -78,6 +78,7 @@ SIGNATURES = {
     "s3_sttsvc_profile": (_I32, [_P, _I32, _P, _P, ctypes.POINTER(s3_profile), _P]),
     "s3_nqz_options_init": (_I32, [ctypes.POINTER(s3_nqz_options)]),
     "s3_hcentrality": (_I32, [_P, ctypes.POINTER(s3_nqz_options), _P, _P, ctypes.POINTER(s3_nqz_result), _P]),
+    "s3_sttsvc_f32_noalloc": (_I32, [_I64, _I64, _I32, _P, _P, _P, _P, _P]),
     "s3_destroy": (_I32, [_P]),
     "s3_last_error": (ctypes.c_char_p, []),
     "s3_status_string": (ctypes.c_char_p, [_I32]),
