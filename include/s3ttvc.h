@@ -90,8 +90,17 @@ typedef struct {
     int32_t thread_max_w;  /* edges whose window N-|e|+1 is <= this use one thread per edge, wider ones
                               one warp per edge; 0 = library default (32), range 1..32 */
     int32_t block_threads; /* threads per block of the thread-per-edge kernels; 0 = default (128) */
-    int32_t reserved[9];
+    int32_t order;         /* order of the nodes inside every edge (the sequence the prefix products
+                              and the CCSS forest follow) and of the edges inside a size bucket:
+                              S3_ORDER_DEGREE (default) = decreasing degree, ties by id, edges sorted
+                              lexicographically; S3_ORDER_INDEX = increasing node id (the index
+                              order of Sec. II-B / Fig. 2), edges in input order */
+    int32_t streams;       /* size buckets are spread over this many CUDA streams forked from the
+                              caller's stream (1..8); 0 = default (4) */
+    int32_t reserved[7];
 } s3_options;
+
+typedef enum { S3_ORDER_DEGREE = 0, S3_ORDER_INDEX = 1 } s3_order;
 
 typedef struct s3_graph_s *s3_graph_t;
 

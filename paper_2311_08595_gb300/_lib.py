@@ -20,6 +20,7 @@ S3_OK, S3_EINVAL, S3_ENOMEM, S3_ECUDA, S3_ENOCONV, S3_ETIMEOUT, S3_ERANGE, S3_EN
 S3_F32, S3_F64 = 0, 1
 S3_REDUCE_SEGMENTED, S3_REDUCE_ATOMIC = 0, 1
 S3_LAYOUT_EDGE, S3_LAYOUT_CCSS = 0, 1
+S3_ORDER_DEGREE, S3_ORDER_INDEX = 0, 1
 
 
 class S3Error(RuntimeError):
@@ -31,7 +32,8 @@ class S3Error(RuntimeError):
 class s3_options(ctypes.Structure):
     _fields_ = [("rank", ctypes.c_int32), ("reduce", ctypes.c_int32), ("layout", ctypes.c_int32),
                 ("build_ccss", ctypes.c_int32), ("device", ctypes.c_int32), ("thread_max_w", ctypes.c_int32),
-                ("block_threads", ctypes.c_int32), ("reserved", ctypes.c_int32 * 9)]
+                ("block_threads", ctypes.c_int32), ("order", ctypes.c_int32), ("streams", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 7)]
 
 
 class s3_format_info(ctypes.Structure):

@@ -1,6 +1,7 @@
 // C ABI entry points: handles, format upload, S^3TTVc orchestration.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 #include <mutex>
@@ -53,6 +54,14 @@ s3_status upload(s3_graph_s *g, T **dst, const std::vector<T> &src) {
 void free_all(s3_graph_s *g) {
     for (void *p : g->allocations) cudaFree(p);
     g->allocations.clear();
+    for (int i = 0; i < 8; ++i) {
+        if (g->aux[i]) cudaStreamDestroy(g->aux[i]);
+        if (g->ev_join[i]) cudaEventDestroy(g->ev_join[i]);
+        g->aux[i] = nullptr;
+        g->ev_join[i] = nullptr;
+    }
+    if (g->ev_fork) cudaEventDestroy(g->ev_fork);
+    g->ev_fork = nullptr;
 }
 
 }  // namespace
@@ -77,8 +86,17 @@ s3_status run_edges(s3_graph_s *g, s3_dtype dt, const void *x, void *y, int bias
         S3_CUDA(cudaMemsetAsync(y, 0, esz * (size_t)g->n, st));
         if (dt == S3_F32) S3_CUDA(cudaMemsetAsync(g->d_comp, 0, sizeof(float) * (size_t)g->n, st));
     }
-    for (size_t k = 0; k < g->buckets.size(); ++k) {
+    // fork: buckets run concurrently on the handle's streams (heaviest first, greedy balance)
+    const int ns = g->n_streams;
+    if (ns > 1) {
+        S3_CUDA(cudaEventRecord(g->ev_fork, st));
+        for (int i = 0; i < ns; ++i) S3_CUDA(cudaStreamWaitEvent(g->aux[i], g->ev_fork, 0));
+    }
+    double load[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    for (size_t r = 0; r < g->bucket_order.size(); ++r) {
+        const size_t k = g->bucket_order[r];
         const HostBucket &hb = g->buckets[k];
+        if (hb.m <= 0) continue;
         EdgeBucketArgs b{};
         b.ids = g->d_ids + hb.offset;
         b.slot = g->d_slot + hb.offset;
@@ -90,11 +108,25 @@ s3_status run_edges(s3_graph_s *g, s3_dtype dt, const void *x, void *y, int bias
         b.K = g->K[k];
         b.Km = g->Km[k];
         b.Ke = g->Ke[k];
+        cudaStream_t bs = st;
+        if (ns > 1) {
+            int best = 0;
+            for (int i = 1; i < ns; ++i)
+                if (load[i] < load[best]) best = i;
+            load[best] += g->bucket_cost[k];
+            bs = g->aux[best];
+        }
         cudaError_t e = dt == S3_F32
-                            ? launch_edge_bucket_f32(b, (const float *)x, o, g->opt.thread_max_w, g->opt.block_threads, st)
-                            : launch_edge_bucket_f64(b, (const double *)x, o, g->opt.thread_max_w, g->opt.block_threads, st);
+                            ? launch_edge_bucket_f32(b, (const float *)x, o, g->opt.thread_max_w, g->opt.block_threads, bs)
+                            : launch_edge_bucket_f64(b, (const double *)x, o, g->opt.thread_max_w, g->opt.block_threads, bs);
         if (e != cudaSuccess) return cuda_fail(e, "edge kernel launch");
-        if (hb.m > 0) ++launches;
+        ++launches;
+    }
+    if (ns > 1) {
+        for (int i = 0; i < ns; ++i) {
+            S3_CUDA(cudaEventRecord(g->ev_join[i], g->aux[i]));
+            S3_CUDA(cudaStreamWaitEvent(st, g->ev_join[i], 0));
+        }
     }
     if (mid) S3_CUDA(cudaEventRecord(mid, st));
     if (seg) {
@@ -141,6 +173,8 @@ s3_status s3_options_init(s3_options *opt) {
     opt->device = -1;
     opt->thread_max_w = 0;
     opt->block_threads = 0;
+    opt->order = S3_ORDER_DEGREE;
+    opt->streams = 0;
     return S3_OK;
 }
 
@@ -172,6 +206,8 @@ s3_status s3_build_format(int64_t n, int64_t m, const int64_t *edge_ptr, const i
     if (o.layout != S3_LAYOUT_EDGE && o.layout != S3_LAYOUT_CCSS) return fail(S3_EINVAL, "bad layout");
     if (o.thread_max_w < 0 || o.thread_max_w > 32) return fail(S3_EINVAL, "thread_max_w must be in 0..32");
     if (o.block_threads < 0 || o.block_threads > 256 || o.block_threads % 32) return fail(S3_EINVAL, "block_threads must be a multiple of 32 up to 256");
+    if (o.streams < 0 || o.streams > 8) return fail(S3_EINVAL, "streams must be in 0..8");
+    if (o.order != S3_ORDER_DEGREE && o.order != S3_ORDER_INDEX) return fail(S3_EINVAL, "bad order");
     HostFormat f;
     try {
         s3_status st = build_host_format(n, m, edge_ptr, members, o, f);
@@ -237,6 +273,26 @@ s3_status s3_build_format(int64_t n, int64_t m, const int64_t *edge_ptr, const i
     if (f.has_ccss) {
         if ((st = upload_ccss(g, f)) != S3_OK) return bail(st);
     }
+    // concurrent size buckets: streams, events, and a cost estimate per bucket
+    g->n_streams = o.streams > 0 ? std::min(o.streams, 8) : 4;
+    if (g->n_streams > 1) {
+        if (cudaEventCreateWithFlags(&g->ev_fork, cudaEventDisableTiming) != cudaSuccess)
+            return bail(cuda_fail(cudaGetLastError(), "cudaEventCreate"));
+        for (int i = 0; i < g->n_streams; ++i) {
+            if (cudaStreamCreateWithFlags(&g->aux[i], cudaStreamNonBlocking) != cudaSuccess ||
+                cudaEventCreateWithFlags(&g->ev_join[i], cudaEventDisableTiming) != cudaSuccess)
+                return bail(cuda_fail(cudaGetLastError(), "cudaStreamCreate"));
+        }
+    }
+    for (size_t k = 0; k < g->buckets.size(); ++k) {
+        const HostBucket &b = g->buckets[k];
+        double W = (double)(g->N - b.s + 1);
+        double fma = b.s >= 3 ? (2.0 * b.s - 5.0) * W * (W + 1) / 2 + b.s * W : 2 * W;
+        g->bucket_cost.push_back((double)b.m * (fma + 60.0 * b.s));
+        g->bucket_order.push_back(k);
+    }
+    std::stable_sort(g->bucket_order.begin(), g->bucket_order.end(),
+                     [&](size_t a, size_t b) { return g->bucket_cost[a] > g->bucket_cost[b]; });
     g->info.device_bytes = g->device_bytes;
     *out = g;
     return S3_OK;

@@ -91,8 +91,21 @@ s3_status build_host_format(int64_t n, int64_t m, const int64_t *edge_ptr, const
     f.N = N;
     f.max_edge = max_edge;
 
-    // index-ordered (sorted) edges; reject repeats
-    std::vector<int32_t> sorted(members, members + nnz);
+    // node order inside edges: by decreasing degree (ties by id), or by id (index order)
+    const bool by_degree = opt.order != S3_ORDER_INDEX;
+    std::vector<int32_t> key_of;  // key_of[v]: position of v in the chosen order
+    if (by_degree) {
+        std::vector<int64_t> deg(n, 0);
+        for (int64_t j = 0; j < nnz; ++j) deg[members[j]]++;
+        std::vector<int32_t> order(n);
+        std::iota(order.begin(), order.end(), 0);
+        std::stable_sort(order.begin(), order.end(), [&](int32_t a, int32_t b) { return deg[a] > deg[b]; });
+        key_of.assign(n, 0);
+        for (int64_t r = 0; r < n; ++r) key_of[order[r]] = (int32_t)r;
+    }
+    // sorted edges (as keys); reject repeats
+    std::vector<int32_t> sorted(nnz);
+    for (int64_t j = 0; j < nnz; ++j) sorted[j] = by_degree ? key_of[members[j]] : members[j];
     for (int64_t e = 0; e < m; ++e) {
         auto b = sorted.begin() + edge_ptr[e], t = sorted.begin() + edge_ptr[e + 1];
         std::sort(b, t);
@@ -101,6 +114,12 @@ s3_status build_host_format(int64_t n, int64_t m, const int64_t *edge_ptr, const
             os << "edge " << e << " repeats a node";
             return fail(S3_EINVAL, os.str());
         }
+    }
+    // back from keys to node ids
+    std::vector<int32_t> node_of_key;
+    if (by_degree) {
+        node_of_key.assign(n, 0);
+        for (int64_t v = 0; v < n; ++v) node_of_key[key_of[v]] = (int32_t)v;
     }
 
     // size buckets
@@ -122,14 +141,26 @@ s3_status build_host_format(int64_t n, int64_t m, const int64_t *edge_ptr, const
     f.ids.assign(off, 0);
     f.slot.assign(off, 0);
     std::vector<int64_t> fillk(N + 1, 0);
-    // position of each edge inside its bucket
-    std::vector<int64_t> pos_in_bucket(m);
-    for (int64_t e = 0; e < m; ++e) {
+    // edges of a bucket: lexicographic by key sequence (degree order) or input order
+    std::vector<int64_t> edge_order(m);
+    std::iota(edge_order.begin(), edge_order.end(), 0);
+    if (by_degree) {
+        std::stable_sort(edge_order.begin(), edge_order.end(), [&](int64_t a, int64_t b) {
+            int64_t sa = edge_ptr[a + 1] - edge_ptr[a], sb = edge_ptr[b + 1] - edge_ptr[b];
+            if (sa != sb) return sa < sb;
+            const int32_t *pa = sorted.data() + edge_ptr[a], *pb = sorted.data() + edge_ptr[b];
+            return std::lexicographical_compare(pa, pa + sa, pb, pb + sb);
+        });
+    }
+    for (int64_t r = 0; r < m; ++r) {
+        int64_t e = edge_order[r];
         int s = (int)(edge_ptr[e + 1] - edge_ptr[e]);
         const HostBucket &b = f.buckets[bucket_of_size[s]];
         int64_t k = fillk[s]++;
-        pos_in_bucket[e] = k;
-        for (int i = 0; i < s; ++i) f.ids[b.offset + (int64_t)i * b.ld + k] = sorted[edge_ptr[e] + i];
+        for (int i = 0; i < s; ++i) {
+            int32_t key = sorted[edge_ptr[e] + i];
+            f.ids[b.offset + (int64_t)i * b.ld + k] = by_degree ? node_of_key[key] : key;
+        }
     }
 
     // node-sorted incidence: slots ordered by node, then bucket, then edge, then member

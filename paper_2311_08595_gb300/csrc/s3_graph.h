@@ -62,6 +62,13 @@ struct s3_graph_s {
     int32_t hist_cap = 0;
 
     int32_t last_launches = 0;       // kernels launched by the last S^3TTVc call
+    // concurrent buckets: forked streams and events, bucket order (heaviest first) and cost
+    int n_streams = 1;
+    cudaStream_t aux[8] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+    cudaEvent_t ev_fork = nullptr;
+    cudaEvent_t ev_join[8] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+    std::vector<size_t> bucket_order;
+    std::vector<double> bucket_cost;
     std::vector<void *> allocations;
     int64_t device_bytes = 0;
 };

@@ -93,7 +93,15 @@ __global__ void __launch_bounds__(kRedThreads) reduce_kernel(ReduceArgs r, const
         int v = r.small_nodes[i];
         int64_t b = r.inc_ptr[v], t = r.inc_ptr[v + 1];
         A a;
-        for (int64_t k = b; k < t; ++k) a.add(buf[k]);
+        int64_t k = b;
+        for (; k + 4 <= t; k += 4) {  // four loads in flight, added in order
+            T v0 = buf[k], v1 = buf[k + 1], v2 = buf[k + 2], v3 = buf[k + 3];
+            a.add(v0);
+            a.add(v1);
+            a.add(v2);
+            a.add(v3);
+        }
+        for (; k < t; ++k) a.add(buf[k]);
         y[v] = (T)a.value();
     } else if (bid < nb_small + nb_med) {
         int64_t i = (bid - nb_small) * (kRedThreads / 32) + (tid >> 5);

@@ -172,46 +172,43 @@ __device__ __forceinline__ void toeplitz_inplace(T (&P)[W], const T (&a)[W]) {
     }
 }
 
+// ---------------------------------------------------------- cp.async ---
+
+__device__ __forceinline__ unsigned smem_addr(const void *p) { return (unsigned)__cvta_generic_to_shared(p); }
+
+// Asynchronous 4- or 8-byte copy global -> shared memory (completion tracked per thread).
+template <int BYTES>
+__device__ __forceinline__ void cp_async(void *smem_dst, const void *gmem_src) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], %2;\n" ::"r"(smem_addr(smem_dst)), "l"(gmem_src),
+                 "n"(BYTES));
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+
 template <typename T>
-__device__ __forceinline__ void emit_thread(const EdgeBucketArgs &b, const EdgeOutArgs &o, int64_t e, int q,
-                                            T val, int p, T xhat) {
+__device__ __forceinline__ void emit_value(const EdgeBucketArgs &b, const EdgeOutArgs &o, int v, int sl, T val,
+                                           int p, T xhat) {
     int bias_e = o.bias ? (Arith<T>::expo(xhat) - p) : 0;
     T c = finalize_value<T>(val, b, p, bias_e, o.range_events);
     if (o.mode == kOutBuffer) {
-        int sl = __ldg(b.slot + (int64_t)q * b.ld + e);
         reinterpret_cast<T *>(o.out)[sl] = c;
     } else {
-        int v = __ldg(b.ids + (int64_t)q * b.ld + e);
         scatter_atomic<T>(o, v, c);
     }
 }
 
-// Shared memory per thread: s values (scaled x) + (s-2) windows of W (Pre_2..Pre_{s-1}),
-// interleaved across the block (element k of thread t at k * blockDim + t).
+// All contributions of one edge.  Xs[i*BS]: the member values (overwritten by
+// their scaled copies); Pre: this thread's column for Pre_2..Pre_{s-1};
+// ib/sb: this thread's member ids / incidence slots (stride BS).
 template <typename T, int W>
-__global__ void __launch_bounds__(256) edge_thread_kernel(EdgeBucketArgs b, const T *__restrict__ x,
-                                                          EdgeOutArgs o) {
-    if (o.skip && *o.skip) return;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    T *sm = reinterpret_cast<T *>(smem_raw);
-    const int BS = blockDim.x;
-    const int tid = threadIdx.x;
-    const int64_t e = (int64_t)blockIdx.x * BS + tid;
-    if (e >= b.m) return;
-    const int s = b.s;
-    T *Xs = sm + tid;
-    T *Pre = sm + (int64_t)s * BS + tid;
-
+__device__ __forceinline__ void edge_compute(const EdgeBucketArgs &b, const EdgeOutArgs &o, T *Xs, T *Pre,
+                                             const int32_t *ib, const int32_t *sb, int BS, int s) {
     T S = T(0);
-    for (int i = 0; i < s; ++i) {
-        int v = __ldg(b.ids + (int64_t)i * b.ld + e);
-        T X = __ldg(x + v);
-        Xs[i * BS] = X;
-        S += Arith<T>::absv(X);
-    }
+    for (int i = 0; i < s; ++i) S += Arith<T>::absv(Xs[i * BS]);
     const int p = scale_exponent<T>(S, b.target);
     const T g = Arith<T>::pow2(p);
     for (int i = 0; i < s; ++i) Xs[i * BS] *= g;
+    const bool buf = o.mode == kOutBuffer;
 
     // forward: P = Pre_2, then Pre_3 .. Pre_s (windows Pre_2..Pre_{s-1} kept in shared memory)
     T P[W];
@@ -229,14 +226,15 @@ __global__ void __launch_bounds__(256) edge_thread_kernel(EdgeBucketArgs b, cons
     T F = T(0);
 #pragma unroll
     for (int j = 0; j <= W - 2; ++j) F = Arith<T>::fma_(P[j], Q[W - 2 - j], F);
-    emit_thread<T>(b, o, e, s - 1, F + P[W - 1], p, Xs[(s - 1) * BS]);
+    emit_value<T>(b, o, buf ? 0 : ib[(s - 1) * BS], buf ? sb[(s - 1) * BS] : 0, F + P[W - 1], p,
+                  Xs[(s - 1) * BS]);
     T top = T(0);
     for (int q = s - 2; q >= 1; --q) {
         // Q = Suf_{q+1}; Pre_{q+1} sits in slot q-1
         T D = T(0);
 #pragma unroll
         for (int j = 0; j < W; ++j) D = Arith<T>::fma_(Pre[((q - 1) * W + j) * BS], Q[W - 1 - j], D);
-        emit_thread<T>(b, o, e, q, F + D, p, Xs[q * BS]);
+        emit_value<T>(b, o, buf ? 0 : ib[q * BS], buf ? sb[q * BS] : 0, F + D, p, Xs[q * BS]);
         T a[W];
         power_table<T, W>(Xs[q * BS], a);
         if (q >= 2) {
@@ -247,7 +245,69 @@ __global__ void __launch_bounds__(256) edge_thread_kernel(EdgeBucketArgs b, cons
         }
     }
     T D1 = (s == 2) ? Q[W - 1] : top;
-    emit_thread<T>(b, o, e, 0, F + D1, p, Xs[0]);
+    emit_value<T>(b, o, buf ? 0 : ib[0], buf ? sb[0] : 0, F + D1, p, Xs[0]);
+}
+
+// Shared memory per thread, interleaved across the block (element k of thread t
+// at k * blockDim + t): Xb[2][s] and Pre[(s-2) W] of T, then Ib[3][s] member ids
+// and Sb[3][s] incidence slots (int32).
+template <typename T>
+__host__ __device__ constexpr size_t thread_smem_words(int s, int W) {
+    return (size_t)(2 * s + (s > 2 ? (s - 2) * W : 0)) * sizeof(T) / 4 + (size_t)6 * s;
+}
+
+// One thread per edge, several edges per thread (grid-stride), software
+// pipelined with cp.async: while edge k is computed, the x gathers of edge k+1
+// and the id/slot loads of edge k+2 are in flight.
+template <typename T, int W>
+__global__ void __launch_bounds__(256) edge_thread_kernel(EdgeBucketArgs b, const T *__restrict__ x,
+                                                          EdgeOutArgs o) {
+    if (o.skip && *o.skip) return;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int BS = blockDim.x;
+    const int tid = threadIdx.x;
+    const int s = b.s;
+    T *tb = reinterpret_cast<T *>(smem_raw);
+    T *Xb0 = tb + tid;
+    T *Xb1 = tb + (size_t)s * BS + tid;
+    T *Pre = tb + (size_t)2 * s * BS + tid;
+    int32_t *ibase = reinterpret_cast<int32_t *>(tb + (size_t)(2 * s + (s > 2 ? (s - 2) * W : 0)) * BS) + tid;
+    const bool need_slot = o.mode == kOutBuffer;
+    const int64_t stride = (int64_t)gridDim.x * BS;
+    int64_t e = (int64_t)blockIdx.x * BS + tid;
+    if (e >= b.m) return;
+
+    auto ids_of = [&](int r) { return ibase + (size_t)r * s * BS; };
+    auto slots_of = [&](int r) { return ibase + (size_t)(3 + r) * s * BS; };
+    auto issue_ids = [&](int64_t ee, int r) {
+        int32_t *ib = ids_of(r), *sb = slots_of(r);
+        for (int i = 0; i < s; ++i) {
+            cp_async<4>(ib + (size_t)i * BS, b.ids + (int64_t)i * b.ld + ee);
+            if (need_slot) cp_async<4>(sb + (size_t)i * BS, b.slot + (int64_t)i * b.ld + ee);
+        }
+    };
+    auto issue_x = [&](int r, T *xb) {
+        const int32_t *ib = ids_of(r);
+        for (int i = 0; i < s; ++i) cp_async<(int)sizeof(T)>(xb + (size_t)i * BS, x + ib[(size_t)i * BS]);
+    };
+
+    issue_ids(e, 0);
+    cp_async_commit();
+    cp_async_wait_all();
+    issue_x(0, Xb0);
+    if (e + stride < b.m) issue_ids(e + stride, 1);
+    cp_async_commit();
+    for (int k = 0; e < b.m; e += stride, ++k) {
+        const int rc = k % 3;
+        T *xc = (k & 1) ? Xb1 : Xb0;
+        T *xn = (k & 1) ? Xb0 : Xb1;
+        cp_async_wait_all();
+        if (e + stride < b.m) issue_x((k + 1) % 3, xn);
+        if (e + 2 * stride < b.m) issue_ids(e + 2 * stride, (k + 2) % 3);
+        cp_async_commit();
+        edge_compute<T, W>(b, o, xc, Pre, ids_of(rc), slots_of(rc), BS, s);
+    }
+    cp_async_wait_all();
 }
 
 // Size-1 edges: c(e, v) = x_v^(N-1) (K(1,N) [t^(N-1)] e^(x t) with K(1,N) = (N-1)!).
@@ -426,9 +486,24 @@ constexpr int kMaxThreadW = 32;
 
 template <typename T, int W>
 cudaError_t launch_thread_w(const EdgeBucketArgs &b, const T *x, const EdgeOutArgs &o, int bs, cudaStream_t st) {
-    size_t per_thread = (size_t)(b.s + (b.s > 2 ? (b.s - 2) * W : 0)) * sizeof(T);
-    size_t smem = per_thread * (size_t)bs;
-    int64_t grid = (b.m + bs - 1) / bs;
+    size_t smem = thread_smem_words<T>(b.s, W) * 4 * (size_t)bs;
+    // enough blocks to fill the GPU (several edges per thread beyond that)
+    static int sms = 0;
+    if (sms == 0) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (sms <= 0) sms = 148;
+    }
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, edge_thread_kernel<T, W>, bs, smem) != cudaSuccess ||
+        per_sm <= 0) {
+        cudaGetLastError();
+        per_sm = 1;
+    }
+    int64_t full = (int64_t)sms * per_sm;
+    int64_t need = (b.m + bs - 1) / bs;
+    int64_t grid = need < full ? need : full;
     edge_thread_kernel<T, W><<<(unsigned)grid, bs, smem, st>>>(b, x, o);
     return cudaGetLastError();
 }
@@ -457,7 +532,7 @@ cudaError_t prepare_edge_kernels_t() {
 // memory stays under kSmemCap; 0 if not even one warp fits.
 template <typename T>
 int thread_block_size(int s, int W, int want) {
-    size_t per_thread = (size_t)(s + (s > 2 ? (s - 2) * W : 0)) * sizeof(T);
+    size_t per_thread = thread_smem_words<T>(s, W) * 4;
     int bs = want;
     while (bs > 32 && per_thread * (size_t)bs > kSmemCap) bs -= 32;
     return per_thread * (size_t)bs > kSmemCap ? 0 : bs;

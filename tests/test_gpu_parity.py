@@ -49,6 +49,8 @@ def test_small_config_all_paths():
     # every window through the warp-per-edge kernel, and small thread blocks
     check(hg, x, reduces=(0,), thread_max_w=1)
     check(hg, x, reduces=(0,), block_threads=32)
+    # index order (no degree sort) and a single stream
+    check(hg, x, reduces=(0, 1), order=1, streams=1, layouts=(None, "ccss"))
 
 
 def test_powerlaw_medium_rank25():

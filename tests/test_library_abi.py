@@ -46,7 +46,7 @@ def test_version_and_status_strings(s3):
 
 def test_inspect_fig1_matches_fig2_counts(s3):
     hg = s3synth.fig1_example()
-    info = s3.s3_format_inspect(hg.n, hg.edge_ptr, hg.members, build_ccss=1)
+    info = s3.s3_format_inspect(hg.n, hg.edge_ptr, hg.members, build_ccss=1, order=1)
     assert info["rank"] == 4 and info["nnz"] == 21 and info["m"] == 6
     assert info["edges_per_size"][2:5] == [1, 1, 4]
     assert info["ccss_nodes_per_level"][1:4] == [6, 10, 16]
@@ -57,7 +57,7 @@ def test_inspect_fig1_matches_fig2_counts(s3):
 @pytest.mark.parametrize("seed", range(6))
 def test_inspect_ccss_matches_oracle_enumeration(s3, seed):
     hg = s3synth.tiny_case(seed=seed, n=9, m=25, rank=5)
-    info = s3.s3_format_inspect(hg.n, hg.edge_ptr, hg.members, build_ccss=1)
+    info = s3.s3_format_inspect(hg.n, hg.edge_ptr, hg.members, build_ccss=1, order=1)
     want = ccss.level_counts(ccss.trimmed_levels(hg.edges()))
     assert info["ccss_nodes_per_level"][1:1 + len(want)] == want
     assert info["ccss_nodes_per_level"][1 + len(want)] == 0
@@ -66,11 +66,25 @@ def test_inspect_ccss_matches_oracle_enumeration(s3, seed):
 
 def test_inspect_sunflower_sharing(s3):
     hg = s3synth.sunflower(petals=50, k=8, core=5, n=400)
-    info = s3.s3_format_inspect(hg.n, hg.edge_ptr, hg.members, build_ccss=1)
+    info = s3.s3_format_inspect(hg.n, hg.edge_ptr, hg.members, build_ccss=1, order=1)
     want = ccss.level_counts(ccss.trimmed_levels(hg.edges()))
     assert info["ccss_nodes_per_level"][1:1 + len(want)] == want
     # shared prefixes make the forest smaller than one path set per edge ((k^2+k-2)/2 nodes each)
     assert info["ccss_nodes"] < 50 * (8 * 8 + 8 - 2) // 2
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_inspect_ccss_degree_order(s3, seed):
+    # the default order sorts the nodes of every edge by decreasing degree (ties by id):
+    # the forest equals the index-order forest of the relabelled hypergraph
+    hg = s3synth.tiny_case(seed=seed, n=10, m=30, rank=5)
+    deg = hg.degrees()
+    order = sorted(range(hg.n), key=lambda v: (-deg[v], v))
+    key = {v: r for r, v in enumerate(order)}
+    relabelled = [tuple(key[v] for v in e) for e in hg.edges()]
+    info = s3.s3_format_inspect(hg.n, hg.edge_ptr, hg.members, build_ccss=1)
+    want = ccss.level_counts(ccss.trimmed_levels(relabelled))
+    assert info["ccss_nodes_per_level"][1:1 + len(want)] == want
 
 
 def test_inspect_buckets_and_degrees(s3):
