@@ -230,6 +230,68 @@ s3_status s3_nqz_options_init(s3_nqz_options *opt);
 s3_status s3_hcentrality(s3_graph_t g, const s3_nqz_options *opt, const double *x0, double *x_out,
                          s3_nqz_result *res, void *stream);
 
+/* -------------------------------------------------------------- batches --- */
+
+typedef struct s3_batch_s *s3_batch_t;
+
+typedef struct {
+    int32_t block_threads;     /* threads per block of the persistent kernels; 0 = 128 */
+    int32_t edges_per_thread;  /* a tile holds block_threads * edges_per_thread edges of one bucket; 0 = 4 */
+    int32_t thread_max_w;      /* windows up to this use one thread per edge, wider ones a warp; 0 = 32 */
+    int32_t use_graph;         /* 1 (default) = replay one captured CUDA graph per call */
+    char cache_path[256];      /* non-empty: s3_batch_autotune appends its choice to this text file */
+    int32_t reserved[8];
+} s3_batch_options;
+
+typedef struct {
+    int32_t block_threads, edges_per_thread, thread_max_w;
+    float ms;
+} s3_tune_candidate;
+
+typedef struct {
+    int32_t block_threads, edges_per_thread, thread_max_w; /* the configuration chosen */
+    int32_t tried;                                         /* configurations timed */
+    float ms;                                              /* its device time per batched call */
+    int32_t reserved;
+    s3_tune_candidate candidates[32];                      /* every configuration timed (first 32) */
+} s3_tune_result;
+
+s3_status s3_batch_options_init(s3_batch_options *opt);
+
+/*
+ * Group `count` graph handles (built with the segmented reduce, same device)
+ * and `nvec` vectors per graph for s3_sttsvc_batched.  The handles must outlive
+ * the batch.  Allocates the per-(graph, vector) buffers and work lists.
+ * graphs: host array of count handles.
+ */
+s3_status s3_batch_create(int32_t count, const s3_graph_t *graphs, int32_t nvec, const s3_batch_options *opt,
+                          s3_batch_t *out);
+
+/*
+ * y_{g,v} = B_g x_{g,v}^(N_g - 1) for every graph g and vector v of the batch,
+ * in one persistent edge kernel, one persistent reduce kernel and one hub
+ * pass, replayed from a captured CUDA graph.  Every edge's member ids and
+ * incidence slots are loaded once for all nvec vectors of its graph.
+ * x, y: HOST arrays of count*nvec DEVICE pointers, graph-major
+ * (x[g*nvec + v] holds n_g elements of dt; y likewise, overwritten).
+ * Results equal nvec*count separate s3_sttsvc calls up to summation order
+ * inside edges (deterministic run to run).  When the pointer arrays differ
+ * from the previous call the call first waits for that call to finish.
+ */
+s3_status s3_sttsvc_batched(s3_batch_t b, s3_dtype dt, const void *const *x, void *const *y, void *stream);
+
+/*
+ * Time candidate configurations (block_threads x edges_per_thread x
+ * thread_max_w) of s3_sttsvc_batched on these inputs (each: one warm-up and
+ * three timed calls, CUDA events on `stream`), keep the fastest for later
+ * calls and report all of them in *res (host).  Synchronous.
+ */
+s3_status s3_batch_autotune(s3_batch_t b, s3_dtype dt, const void *const *x, void *const *y, s3_tune_result *res,
+                            void *stream);
+
+/* Release a batch (not its graphs).  NULL is allowed. */
+s3_status s3_batch_destroy(s3_batch_t b);
+
 /* ----------------------------------------------- allocation-free call --- */
 
 /* Largest node count s3_sttsvc_f32_noalloc accepts (its fixed scratch: 4 bytes per node). */

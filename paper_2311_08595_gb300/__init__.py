@@ -27,6 +27,8 @@ __all__ = [
     "Graph", "S3Error", "s3_options_init", "s3_format_inspect", "s3_build_format", "s3_graph_query",
     "s3_sttsvc", "s3_sttsvc_layout", "s3_sttsvc_host", "s3_sttsvc_profile", "s3_range_events", "s3_hcentrality",
     "s3_nqz_options_init", "s3_sttsvc_f32_noalloc", "s3_destroy", "s3_version", "lib_path",
+    "Batch", "s3_batch_options_init", "s3_batch_create", "s3_sttsvc_batched", "s3_batch_autotune",
+    "s3_batch_destroy",
 ]
 
 
@@ -212,6 +214,79 @@ def s3_sttsvc_f32_noalloc(n, edge_ptr, members, x, y, rank, stream=None):
     check(load().s3_sttsvc_f32_noalloc(int(n), edge_ptr.numel() - 1, int(rank), ptr(edge_ptr), ptr(members),
                                        ptr(x), ptr(y), _stream(stream)))
     return y
+
+
+class Batch:
+    """Owns an s3_batch_t (keeps its graphs alive); released by s3_batch_destroy."""
+
+    def __init__(self, handle, graphs, nvec):
+        self.handle = handle
+        self.graphs = list(graphs)
+        self.nvec = nvec
+
+    def __del__(self):
+        try:
+            s3_batch_destroy(self)
+        except Exception:
+            pass
+
+
+def s3_batch_options_init(**kw):
+    o = _lib.s3_batch_options()
+    check(load().s3_batch_options_init(ctypes.byref(o)))
+    for k, v in kw.items():
+        if k == "cache_path":
+            o.cache_path = v.encode()
+        elif hasattr(o, k):
+            setattr(o, k, int(v))
+        else:
+            raise TypeError(f"unknown batch option {k}")
+    return o
+
+
+def s3_batch_create(graphs, nvec, **kw):
+    o = s3_batch_options_init(**kw)
+    arr = (ctypes.c_void_p * len(graphs))(*[g.handle for g in graphs])
+    h = ctypes.c_void_p()
+    check(load().s3_batch_create(len(graphs), arr, int(nvec), ctypes.byref(o), ctypes.byref(h)))
+    return Batch(h, graphs, nvec)
+
+
+def _ptr_arrays(b, xs, ys):
+    """xs, ys: lists (graph-major, len count*nvec) of CUDA tensors -> host pointer arrays."""
+    J = len(b.graphs) * b.nvec
+    if len(xs) != J or len(ys) != J:
+        raise ValueError(f"need {J} x and y tensors (graph-major)")
+    for j, (x, y) in enumerate(zip(xs, ys)):
+        g = b.graphs[j // b.nvec]
+        _check_vec(g, x, "x")
+        _check_vec(g, y, "y")
+    code = _dtype_code(xs[0])
+    xa = (ctypes.c_void_p * J)(*[t.data_ptr() for t in xs])
+    ya = (ctypes.c_void_p * J)(*[t.data_ptr() for t in ys])
+    return code, xa, ya
+
+
+def s3_sttsvc_batched(b, xs, ys, stream=None):
+    code, xa, ya = _ptr_arrays(b, xs, ys)
+    check(load().s3_sttsvc_batched(b.handle, code, xa, ya, _stream(stream)))
+    return ys
+
+
+def s3_batch_autotune(b, xs, ys, stream=None):
+    code, xa, ya = _ptr_arrays(b, xs, ys)
+    r = _lib.s3_tune_result()
+    check(load().s3_batch_autotune(b.handle, code, xa, ya, ctypes.byref(r), _stream(stream)))
+    cands = [{"block_threads": c.block_threads, "edges_per_thread": c.edges_per_thread,
+              "thread_max_w": c.thread_max_w, "ms": c.ms} for c in r.candidates[:min(r.tried, 32)]]
+    return {"block_threads": r.block_threads, "edges_per_thread": r.edges_per_thread,
+            "thread_max_w": r.thread_max_w, "ms": r.ms, "tried": r.tried, "candidates": cands}
+
+
+def s3_batch_destroy(b):
+    if b is not None and getattr(b, "handle", None):
+        h, b.handle = b.handle, None
+        check(load().s3_batch_destroy(h))
 
 
 def s3_destroy(g):

@@ -63,6 +63,23 @@ class s3_profile(ctypes.Structure):
                 ("launches", ctypes.c_int32), ("reserved", ctypes.c_int32 * 4)]
 
 
+class s3_batch_options(ctypes.Structure):
+    _fields_ = [("block_threads", ctypes.c_int32), ("edges_per_thread", ctypes.c_int32),
+                ("thread_max_w", ctypes.c_int32), ("use_graph", ctypes.c_int32),
+                ("cache_path", ctypes.c_char * 256), ("reserved", ctypes.c_int32 * 8)]
+
+
+class s3_tune_candidate(ctypes.Structure):
+    _fields_ = [("block_threads", ctypes.c_int32), ("edges_per_thread", ctypes.c_int32),
+                ("thread_max_w", ctypes.c_int32), ("ms", ctypes.c_float)]
+
+
+class s3_tune_result(ctypes.Structure):
+    _fields_ = [("block_threads", ctypes.c_int32), ("edges_per_thread", ctypes.c_int32),
+                ("thread_max_w", ctypes.c_int32), ("tried", ctypes.c_int32), ("ms", ctypes.c_float),
+                ("reserved", ctypes.c_int32), ("candidates", s3_tune_candidate * 32)]
+
+
 _P = ctypes.c_void_p
 _I64 = ctypes.c_int64
 _I32 = ctypes.c_int32
@@ -81,6 +98,11 @@ SIGNATURES = {
     "s3_nqz_options_init": (_I32, [ctypes.POINTER(s3_nqz_options)]),
     "s3_hcentrality": (_I32, [_P, ctypes.POINTER(s3_nqz_options), _P, _P, ctypes.POINTER(s3_nqz_result), _P]),
     "s3_sttsvc_f32_noalloc": (_I32, [_I64, _I64, _I32, _P, _P, _P, _P, _P]),
+    "s3_batch_options_init": (_I32, [ctypes.POINTER(s3_batch_options)]),
+    "s3_batch_create": (_I32, [_I32, _P, _I32, ctypes.POINTER(s3_batch_options), ctypes.POINTER(_P)]),
+    "s3_sttsvc_batched": (_I32, [_P, _I32, _P, _P, _P]),
+    "s3_batch_autotune": (_I32, [_P, _I32, _P, _P, ctypes.POINTER(s3_tune_result), _P]),
+    "s3_batch_destroy": (_I32, [_P]),
     "s3_destroy": (_I32, [_P]),
     "s3_last_error": (ctypes.c_char_p, []),
     "s3_status_string": (ctypes.c_char_p, [_I32]),

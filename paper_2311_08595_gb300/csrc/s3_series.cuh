@@ -366,17 +366,12 @@ __device__ __forceinline__ void power_table_warp(T X, T *out, int W) {
     }
 }
 
-// Per warp shared memory (elements of T): Xs[s] | C[s] | Pre[(s-2) W] (Pre_2..Pre_{s-1}) |
-// Pcur[W] | Q[W] | A[W] | R[W].  One edge per warp, grid-stride over the bucket.
+// One edge computed by one warp.  Per warp shared memory (elements of T): Xs[s] | C[s] |
+// Pre[(s-2) W] (Pre_2..Pre_{s-1}) | Pcur[W] | Q[W] | A[W] | R[W].
 template <typename T>
-__global__ void __launch_bounds__(128) edge_warp_kernel(EdgeBucketArgs b, const T *__restrict__ x, EdgeOutArgs o,
-                                                        int W, int64_t per_warp) {
-    if (o.skip && *o.skip) return;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
+__device__ __forceinline__ void warp_edge_compute(const EdgeBucketArgs &b, const T *__restrict__ x,
+                                                  const EdgeOutArgs &o, int64_t e, int W, T *base) {
     const int lane = threadIdx.x & 31;
-    const int wib = threadIdx.x >> 5;
-    const int wpb = blockDim.x >> 5;
-    T *base = reinterpret_cast<T *>(smem_raw) + (int64_t)wib * per_warp;
     const int s = b.s;
     T *Xs = base;
     T *C = Xs + s;
@@ -385,93 +380,106 @@ __global__ void __launch_bounds__(128) edge_warp_kernel(EdgeBucketArgs b, const 
     T *Q = Pc + W;
     T *A = Q + W;
     T *R = A + W;
-    for (int64_t e = (int64_t)blockIdx.x * wpb + wib; e < b.m; e += (int64_t)gridDim.x * wpb) {
-        T part = T(0);
-        for (int i = lane; i < s; i += 32) {
-            T X = __ldg(x + __ldg(b.ids + (int64_t)i * b.ld + e));
-            Xs[i] = X;
-            part += Arith<T>::absv(X);
+    T part = T(0);
+    for (int i = lane; i < s; i += 32) {
+        T X = __ldg(x + __ldg(b.ids + (int64_t)i * b.ld + e));
+        Xs[i] = X;
+        part += Arith<T>::absv(X);
+    }
+    T S = warp_sum(part);
+    const int p = scale_exponent<T>(S, b.target);
+    const T g = Arith<T>::pow2(p);
+    __syncwarp();
+    for (int i = lane; i < s; i += 32) Xs[i] *= g;
+    __syncwarp();
+    // forward
+    power_table_warp<T>(Xs[0], Pc, W);
+    __syncwarp();
+    for (int i = 1; i <= s - 2; ++i) {
+        T *slotp = Pre + (int64_t)(i - 1) * W;
+        for (int j = lane; j < W; j += 32) slotp[j] = Pc[j];
+        power_table_warp<T>(Xs[i], A, W);
+        __syncwarp();
+        for (int j = lane; j < W; j += 32) {
+            T acc = T(0);
+            for (int jp = 0; jp <= j; ++jp) acc = Arith<T>::fma_(A[j - jp], slotp[jp], acc);
+            Pc[j] = acc;
         }
-        T S = warp_sum(part);
-        const int p = scale_exponent<T>(S, b.target);
-        const T g = Arith<T>::pow2(p);
         __syncwarp();
-        for (int i = lane; i < s; i += 32) Xs[i] *= g;
+    }
+    // backward
+    power_table_warp<T>(Xs[s - 1], Q, W);
+    __syncwarp();
+    T fp = T(0);
+    for (int j = lane; j <= W - 2; j += 32) fp = Arith<T>::fma_(Pc[j], Q[W - 2 - j], fp);
+    const T F = warp_sum(fp);
+    if (lane == 0) C[s - 1] = F + Pc[W - 1];
+    T top = T(0);
+    for (int q = s - 2; q >= 1; --q) {
+        const T *pre = Pre + (int64_t)(q - 1) * W;
+        T dp = T(0);
+        for (int j = lane; j < W; j += 32) dp = Arith<T>::fma_(pre[j], Q[W - 1 - j], dp);
+        T D = warp_sum(dp);
+        if (lane == 0) C[q] = F + D;
+        power_table_warp<T>(Xs[q], A, W);
         __syncwarp();
-        // forward
-        power_table_warp<T>(Xs[0], Pc, W);
-        __syncwarp();
-        for (int i = 1; i <= s - 2; ++i) {
-            T *slotp = Pre + (int64_t)(i - 1) * W;
-            for (int j = lane; j < W; j += 32) slotp[j] = Pc[j];
-            power_table_warp<T>(Xs[i], A, W);
-            __syncwarp();
+        if (q >= 2) {
             for (int j = lane; j < W; j += 32) {
                 T acc = T(0);
-                for (int jp = 0; jp <= j; ++jp) acc = Arith<T>::fma_(A[j - jp], slotp[jp], acc);
-                Pc[j] = acc;
+                for (int jp = 0; jp <= j; ++jp) acc = Arith<T>::fma_(A[j - jp], Q[jp], acc);
+                R[j] = acc;
             }
             __syncwarp();
+            T *t = Q;
+            Q = R;
+            R = t;
+        } else {
+            T tp = T(0);
+            for (int jp = lane; jp < W; jp += 32) tp = Arith<T>::fma_(A[W - 1 - jp], Q[jp], tp);
+            top = warp_sum(tp);
         }
-        // backward
-        power_table_warp<T>(Xs[s - 1], Q, W);
-        __syncwarp();
-        T fp = T(0);
-        for (int j = lane; j <= W - 2; j += 32) fp = Arith<T>::fma_(Pc[j], Q[W - 2 - j], fp);
-        const T F = warp_sum(fp);
-        if (lane == 0) C[s - 1] = F + Pc[W - 1];
-        T top = T(0);
-        for (int q = s - 2; q >= 1; --q) {
-            const T *pre = Pre + (int64_t)(q - 1) * W;
-            T dp = T(0);
-            for (int j = lane; j < W; j += 32) dp = Arith<T>::fma_(pre[j], Q[W - 1 - j], dp);
-            T D = warp_sum(dp);
-            if (lane == 0) C[q] = F + D;
-            power_table_warp<T>(Xs[q], A, W);
-            __syncwarp();
-            if (q >= 2) {
-                for (int j = lane; j < W; j += 32) {
-                    T acc = T(0);
-                    for (int jp = 0; jp <= j; ++jp) acc = Arith<T>::fma_(A[j - jp], Q[jp], acc);
-                    R[j] = acc;
-                }
-                __syncwarp();
-                T *t = Q;
-                Q = R;
-                R = t;
-            } else {
-                T tp = T(0);
-                for (int jp = lane; jp < W; jp += 32) tp = Arith<T>::fma_(A[W - 1 - jp], Q[jp], tp);
-                top = warp_sum(tp);
-            }
-        }
-        if (lane == 0) C[0] = F + (s == 2 ? Q[W - 1] : top);
-        __syncwarp();
-        for (int q = lane; q < s; q += 32) {
-            int bias_e = o.bias ? (Arith<T>::expo(Xs[q]) - p) : 0;
-            T c = finalize_value<T>(C[q], b, p, bias_e, o.range_events);
-            if (o.mode == kOutBuffer) {
-                reinterpret_cast<T *>(o.out)[__ldg(b.slot + (int64_t)q * b.ld + e)] = c;
-            } else {
-                int v = __ldg(b.ids + (int64_t)q * b.ld + e);
-                if constexpr (sizeof(T) == 8) {
-                    atomicAdd(reinterpret_cast<double *>(o.out) + v, (double)c);
-                } else {
-                    float *y = reinterpret_cast<float *>(o.out);
-                    float old = atomicAdd(y + v, (float)c);
-                    if (o.mode == kOutAtomicComp) {
-                        float sm, er;
-                        two_sum(old, (float)c, sm, er);
-                        if (er != 0.f) atomicAdd(o.comp + v, er);
-                    }
-                }
-            }
-        }
-        __syncwarp();
-        // Q/R may have been swapped; restore the fixed layout for the next edge
-        Q = Pc + W;
-        R = A + W;
     }
+    if (lane == 0) C[0] = F + (s == 2 ? Q[W - 1] : top);
+    __syncwarp();
+    for (int q = lane; q < s; q += 32) {
+        int bias_e = o.bias ? (Arith<T>::expo(Xs[q]) - p) : 0;
+        T c = finalize_value<T>(C[q], b, p, bias_e, o.range_events);
+        if (o.mode == kOutBuffer) {
+            reinterpret_cast<T *>(o.out)[__ldg(b.slot + (int64_t)q * b.ld + e)] = c;
+        } else {
+            int v = __ldg(b.ids + (int64_t)q * b.ld + e);
+            if constexpr (sizeof(T) == 8) {
+                atomicAdd(reinterpret_cast<double *>(o.out) + v, (double)c);
+            } else {
+                float *y = reinterpret_cast<float *>(o.out);
+                float old = atomicAdd(y + v, (float)c);
+                if (o.mode == kOutAtomicComp) {
+                    float sm, er;
+                    two_sum(old, (float)c, sm, er);
+                    if (er != 0.f) atomicAdd(o.comp + v, er);
+                }
+            }
+        }
+    }
+    __syncwarp();
+}
+
+// Elements of T per warp for warp_edge_compute.
+__host__ __device__ constexpr int64_t warp_smem_elems(int s, int W) {
+    return ((2 * (int64_t)s + (int64_t)(s > 2 ? s - 2 : 0) * W + 4 * (int64_t)W) + 3) / 4 * 4;
+}
+
+// One edge per warp, grid-stride over the bucket.
+template <typename T>
+__global__ void __launch_bounds__(128) edge_warp_kernel(EdgeBucketArgs b, const T *__restrict__ x, EdgeOutArgs o,
+                                                        int W, int64_t per_warp) {
+    if (o.skip && *o.skip) return;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int wib = threadIdx.x >> 5;
+    const int wpb = blockDim.x >> 5;
+    T *base = reinterpret_cast<T *>(smem_raw) + (int64_t)wib * per_warp;
+    for (int64_t e = (int64_t)blockIdx.x * wpb + wib; e < b.m; e += (int64_t)gridDim.x * wpb)
+        warp_edge_compute<T>(b, x, o, e, W, base);
 }
 
 }  // namespace s3
@@ -563,8 +571,7 @@ cudaError_t launch_edge_bucket_t(const EdgeBucketArgs &b, const T *x, const Edge
         }
     }
     // one warp per edge
-    int64_t per_warp = 2 * (int64_t)b.s + (int64_t)(b.s > 2 ? b.s - 2 : 0) * W + 4 * (int64_t)W;
-    per_warp = (per_warp + 3) / 4 * 4;
+    int64_t per_warp = warp_smem_elems(b.s, W);
     int wpb = 4;
     while (wpb > 1 && (size_t)wpb * per_warp * sizeof(T) > kSmemCapWarp) wpb /= 2;
     size_t smem = (size_t)wpb * per_warp * sizeof(T);
