@@ -32,6 +32,8 @@
 namespace s3 {
 namespace {
 
+constexpr int kBatchClasses = 4;
+
 struct BatchBucket {
     EdgeBucketArgs b;
     int32_t graph;
@@ -382,7 +384,7 @@ struct s3_batch_s {
     void **d_xs = nullptr, **d_ys = nullptr, **d_bufs = nullptr, **d_parts = nullptr;
     void **h_ptrs = nullptr;  // pinned staging: xs then ys
     bool staged = false;
-    unsigned long long *d_counters = nullptr;  // [0] edge tiles, [1] reduce tiles
+    unsigned long long *d_counters = nullptr;  // [0..kBatchClasses) edge tile classes, [kBatchClasses] reduce
     void *d_buf_mem[2] = {nullptr, nullptr};   // per dtype: all per-(graph, vector) buffers
     void *d_part_mem = nullptr;
     std::vector<int64_t> buf_off;              // element offset of each (graph, vector) buffer
@@ -390,6 +392,12 @@ struct s3_batch_s {
     int64_t buf_elems = 0, part_elems = 0;
     size_t smem = 0;
     int built_eb = 0, built_cfg = -1;
+    struct Cls {
+        int64_t begin = 0, end = 0;
+        size_t smem = 0;
+    } cls[kBatchClasses];
+    cudaStream_t aux[kBatchClasses] = {nullptr, nullptr, nullptr, nullptr};
+    cudaEvent_t ev_fork = nullptr, ev_join[kBatchClasses] = {nullptr, nullptr, nullptr, nullptr};
     cudaGraphExec_t exec[2] = {nullptr, nullptr};
     cudaStream_t cap_stream = nullptr;
     std::vector<BatchBucket> h_buckets;
@@ -408,6 +416,17 @@ s3_status batch_alloc(s3_batch_s *bt, void **p, size_t bytes) {
     }
     bt->allocations.push_back(*p);
     return S3_OK;
+}
+
+void free_streams(s3_batch_s *bt) {
+    for (int c = 0; c < kBatchClasses; ++c) {
+        if (bt->aux[c]) cudaStreamDestroy(bt->aux[c]);
+        if (bt->ev_join[c]) cudaEventDestroy(bt->ev_join[c]);
+        bt->aux[c] = nullptr;
+        bt->ev_join[c] = nullptr;
+    }
+    if (bt->ev_fork) cudaEventDestroy(bt->ev_fork);
+    bt->ev_fork = nullptr;
 }
 
 void drop_graphs(s3_batch_s *bt) {
@@ -459,30 +478,54 @@ s3_status build_tiles(s3_batch_s *bt, int elem_bytes) {
         }
     }
     if (smem > 200 * 1024) return fail(S3_ENOTSUP, "batched tile needs more than 200 KiB of shared memory");
-    // warp tiles need per_warp elements for the widest bucket among them
-    int32_t per_warp = 0;
-    for (auto &bb : bt->h_buckets)
-        if (bb.warp == 1) per_warp = std::max<int32_t>(per_warp, (int32_t)warp_smem_elems(bb.b.s, bb.W));
-    std::vector<Tile> tiles;
-    std::vector<double> cost;
+    // tiles are grouped into shared-memory classes, one persistent kernel each (run
+    // concurrently), so that tiles of small edges are not held to the occupancy of the
+    // widest tile; per-thread byte limits of the classes:
+    const size_t class_limit[kBatchClasses] = {128, 320, 768, (size_t)1 << 40};
+    std::vector<int> bucket_class(bt->h_buckets.size(), 0);
+    std::vector<size_t> class_smem(kBatchClasses, 0);
+    for (size_t bi = 0; bi < bt->h_buckets.size(); ++bi) {
+        const BatchBucket &bb = bt->h_buckets[bi];
+        size_t per_block;
+        if (bb.warp == 2) per_block = 0;
+        else if (bb.warp == 1) per_block = (size_t)(bs / 32) * (size_t)warp_smem_elems(bb.b.s, bb.W) * elem_bytes;
+        else per_block = ((size_t)(2 * bb.b.s + (bb.b.s > 2 ? (bb.b.s - 2) * bb.W : 0)) * elem_bytes +
+                          (size_t)24 * bb.b.s) * bs;
+        const size_t per_thread = per_block / bs;
+        int c = 0;
+        while (c < kBatchClasses - 1 && per_thread > class_limit[c]) ++c;
+        // every warp tile indexes its warp's region with the largest per-warp size, so all
+        // warp tiles share the last class, whose reservation covers that size
+        if (bb.warp == 1) c = kBatchClasses - 1;
+        bucket_class[bi] = c;
+        class_smem[c] = std::max(class_smem[c], per_block);
+    }
+    std::vector<std::vector<Tile>> tiles(kBatchClasses);
+    std::vector<std::vector<double>> cost(kBatchClasses);
     const int64_t span = (int64_t)bs * bt->ept;
     for (size_t bi = 0; bi < bt->h_buckets.size(); ++bi) {
         const BatchBucket &bb = bt->h_buckets[bi];
+        const int c = bucket_class[bi];
         const int64_t step = bb.warp == 1 ? (int64_t)(bs / 32) * bt->ept : span;
         for (int64_t e0 = 0; e0 < bb.b.m; e0 += step) {
             Tile t{};
             t.bucket = (int32_t)bi;
             t.e0 = e0;
             t.count = (int32_t)std::min<int64_t>(step, bb.b.m - e0);
-            tiles.push_back(t);
-            cost.push_back(bt->bucket_cost[bi] * t.count);
+            tiles[c].push_back(t);
+            cost[c].push_back(bt->bucket_cost[bi] * t.count);
         }
     }
-    std::vector<size_t> order(tiles.size());
-    for (size_t i = 0; i < order.size(); ++i) order[i] = i;
-    std::stable_sort(order.begin(), order.end(), [&](size_t a, size_t b) { return cost[a] > cost[b]; });
-    std::vector<Tile> sorted(tiles.size());
-    for (size_t i = 0; i < order.size(); ++i) sorted[i] = tiles[order[i]];
+    std::vector<Tile> sorted;
+    for (int c = 0; c < kBatchClasses; ++c) {
+        std::vector<size_t> order(tiles[c].size());
+        for (size_t i = 0; i < order.size(); ++i) order[i] = i;
+        std::stable_sort(order.begin(), order.end(), [&](size_t a, size_t b) { return cost[c][a] > cost[c][b]; });
+        bt->cls[c].begin = (int64_t)sorted.size();
+        for (size_t i = 0; i < order.size(); ++i) sorted.push_back(tiles[c][order[i]]);
+        bt->cls[c].end = (int64_t)sorted.size();
+        bt->cls[c].smem = class_smem[c];
+    }
     // upload
     if ((int64_t)sorted.size() > bt->tiles_cap) {
         void *p = nullptr;
@@ -506,7 +549,6 @@ s3_status build_tiles(s3_batch_s *bt, int elem_bytes) {
     bt->smem = smem;
     bt->built_eb = elem_bytes;
     bt->built_cfg = (bt->bs << 16) ^ (bt->ept << 8) ^ bt->thread_max_w;
-    (void)per_warp;
     return S3_OK;
 }
 
@@ -537,26 +579,38 @@ s3_status record_batch(s3_batch_s *bt, cudaStream_t st) {
     // pointer tables: xs, ys from the pinned staging; buffers and partials
     const size_t J = bt->graphs.size() * (size_t)bt->nvec;
     S3_CUDA(cudaMemcpyAsync(bt->d_xs, bt->h_ptrs, sizeof(void *) * 2 * J, cudaMemcpyHostToDevice, st));
-    S3_CUDA(cudaMemsetAsync(bt->d_counters, 0, 2 * sizeof(unsigned long long), st));
-    BatchEdgeArgs ea{};
-    ea.buckets = bt->d_buckets;
-    ea.tiles = bt->d_tiles;
-    ea.ntiles = bt->ntiles;
-    ea.xs = bt->d_xs;
-    ea.bufs = bt->d_bufs + which * J;
-    ea.nvec = bt->nvec;
+    S3_CUDA(cudaMemsetAsync(bt->d_counters, 0, (kBatchClasses + 1) * sizeof(unsigned long long), st));
     int32_t per_warp = 0;
     for (auto &bb : bt->h_buckets)
         if (bb.warp == 1) per_warp = std::max<int32_t>(per_warp, (int32_t)warp_smem_elems(bb.b.s, bb.W));
-    ea.per_warp = per_warp;
-    ea.counter = bt->d_counters;
-    ea.range_events = bt->graphs.empty() ? nullptr : bt->graphs[0]->d_range;
-    int per_sm = 0;
-    S3_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_edge_kernel<T>, bt->bs, bt->smem));
-    if (per_sm <= 0) return fail(S3_ENOTSUP, "batched kernel does not fit on an SM with this configuration");
-    int grid = (int)std::min<int64_t>((int64_t)bt->sms * per_sm, std::max<int64_t>(bt->ntiles, 1));
-    batch_edge_kernel<T><<<grid, bt->bs, bt->smem, st>>>(ea);
-    S3_CUDA(cudaGetLastError());
+    // fork: one persistent kernel per shared-memory class
+    S3_CUDA(cudaEventRecord(bt->ev_fork, st));
+    for (int c = 0; c < kBatchClasses; ++c) {
+        const int64_t nt = bt->cls[c].end - bt->cls[c].begin;
+        cudaStream_t cs = bt->aux[c];
+        S3_CUDA(cudaStreamWaitEvent(cs, bt->ev_fork, 0));
+        if (nt > 0) {
+            BatchEdgeArgs ea{};
+            ea.buckets = bt->d_buckets;
+            ea.tiles = bt->d_tiles + bt->cls[c].begin;
+            ea.ntiles = nt;
+            ea.xs = bt->d_xs;
+            ea.bufs = bt->d_bufs + which * J;
+            ea.nvec = bt->nvec;
+            ea.per_warp = per_warp;
+            ea.counter = bt->d_counters + c;
+            ea.range_events = bt->graphs.empty() ? nullptr : bt->graphs[0]->d_range;
+            int per_sm = 0;
+            S3_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_edge_kernel<T>, bt->bs,
+                                                                  bt->cls[c].smem));
+            if (per_sm <= 0) return fail(S3_ENOTSUP, "batched kernel does not fit on an SM with this configuration");
+            int grid = (int)std::min<int64_t>((int64_t)bt->sms * per_sm, nt);
+            batch_edge_kernel<T><<<grid, bt->bs, bt->cls[c].smem, cs>>>(ea);
+            S3_CUDA(cudaGetLastError());
+        }
+        S3_CUDA(cudaEventRecord(bt->ev_join[c], cs));
+        S3_CUDA(cudaStreamWaitEvent(st, bt->ev_join[c], 0));
+    }
     BatchReduceArgs ra{};
     ra.graphs = bt->d_rgraphs;
     ra.tiles = bt->d_rtiles;
@@ -567,7 +621,7 @@ s3_status record_batch(s3_batch_s *bt, cudaStream_t st) {
     ra.ys = bt->d_ys;
     ra.partials = bt->d_parts;
     ra.nvec = bt->nvec;
-    ra.counter = bt->d_counters + 1;
+    ra.counter = bt->d_counters + kBatchClasses;
     int rper = 0;
     S3_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&rper, batch_reduce_kernel<T>, 256, 0));
     int rgrid = (int)std::min<int64_t>((int64_t)bt->sms * std::max(rper, 1), std::max<int64_t>(bt->nrtiles, 1));
@@ -664,12 +718,19 @@ s3_status s3_batch_create(int32_t count, const s3_graph_t *graphs, int32_t nvec,
     bt->thread_max_w = opt.thread_max_w > 0 ? std::min(opt.thread_max_w, 32) : 32;
     auto bail = [&](s3_status s) {
         drop_graphs(bt);
+        free_streams(bt);
         for (void *p : bt->allocations) cudaFree(p);
         if (bt->h_ptrs) cudaFreeHost(bt->h_ptrs);
         delete bt;
         return s;
     };
     if (bt->bs % 32 || bt->bs > 256) return bail(fail(S3_EINVAL, "block_threads must be a multiple of 32 up to 256"));
+    if (cudaEventCreateWithFlags(&bt->ev_fork, cudaEventDisableTiming) != cudaSuccess)
+        return bail(cuda_fail(cudaGetLastError(), "cudaEventCreate"));
+    for (int c = 0; c < kBatchClasses; ++c)
+        if (cudaStreamCreateWithFlags(&bt->aux[c], cudaStreamNonBlocking) != cudaSuccess ||
+            cudaEventCreateWithFlags(&bt->ev_join[c], cudaEventDisableTiming) != cudaSuccess)
+            return bail(cuda_fail(cudaGetLastError(), "cudaStreamCreate"));
     if (cudaDeviceGetAttribute(&bt->sms, cudaDevAttrMultiProcessorCount, bt->device) != cudaSuccess)
         return bail(cuda_fail(cudaGetLastError(), "cudaDeviceGetAttribute"));
     s3_status s = S3_OK;
@@ -703,7 +764,7 @@ s3_status s3_batch_create(int32_t count, const s3_graph_t *graphs, int32_t nvec,
         if (cudaMemcpy(bt->d_parts, parts.data(), sizeof(void *) * J, cudaMemcpyHostToDevice) != cudaSuccess)
             return bail(cuda_fail(cudaGetLastError(), "cudaMemcpy"));
     }
-    if ((s = batch_alloc(bt, &p, 2 * sizeof(unsigned long long))) != S3_OK) return bail(s);
+    if ((s = batch_alloc(bt, &p, (kBatchClasses + 1) * sizeof(unsigned long long))) != S3_OK) return bail(s);
     bt->d_counters = reinterpret_cast<unsigned long long *>(p);
     if (cudaHostAlloc(reinterpret_cast<void **>(&bt->h_ptrs), sizeof(void *) * J * 2, cudaHostAllocDefault) !=
         cudaSuccess)
@@ -849,6 +910,7 @@ s3_status s3_batch_destroy(s3_batch_t bt) {
         DeviceGuard guard(bt->device);
         cudaDeviceSynchronize();
         drop_graphs(bt);
+        free_streams(bt);
         if (bt->cap_stream) cudaStreamDestroy(bt->cap_stream);
         for (void *p : bt->allocations) cudaFree(p);
         if (bt->h_ptrs) cudaFreeHost(bt->h_ptrs);
