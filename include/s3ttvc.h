@@ -292,6 +292,66 @@ s3_status s3_batch_autotune(s3_batch_t b, s3_dtype dt, const void *const *x, voi
 /* Release a batch (not its graphs).  NULL is allowed. */
 s3_status s3_batch_destroy(s3_batch_t b);
 
+/* ------------------------------------------------- learned warm start --- */
+
+/* Per-node features and the 12-64-64-1 MLP of the warm start (no counterpart in the paper: it
+ * speeds up Algorithm 1 by starting it near its fixed point; the uniform start stays the
+ * fallback and the reference). */
+#define S3_MLP_FEATURES 12
+#define S3_MLP_HIDDEN 64
+#define S3_MLP_PARAMS 5057   /* W1[64][12] b1[64] W2[64][64] b2[64] W3[64] b3, row-major */
+
+typedef struct s3_mlp_s *s3_mlp_t;
+
+/*
+ * feat: device, n x 12 floats, row-major, written.  Features of node v, each
+ * log1p(.)-scaled: degree; mean and max size of the edges containing v; the
+ * 8-bin histogram of those sizes (bin b collects sizes s with
+ * floor(8 log(s/2)/log(N/2)) = b, clamped to 0..7); the sum over v's edges of
+ * the other members' degrees.  Integer accumulation: bit-reproducible.
+ */
+s3_status s3_features(s3_graph_t g, float *feat, void *stream);
+
+/* New model on the current device.  params: host, S3_MLP_PARAMS floats (FP32
+ * master weights), or NULL for a deterministic He-style initialisation from seed. */
+s3_status s3_mlp_create(const float *params, uint64_t seed, s3_mlp_t *out);
+
+/* Copy the FP32 master weights (bf16 = 0) or their BF16 copies widened to FP32
+ * (bf16 = 1) to params (host, S3_MLP_PARAMS floats).  Synchronises the device. */
+s3_status s3_mlp_get_params(s3_mlp_t m, float *params, int32_t bf16);
+
+/* out[v] = W3 relu(W2 relu(W1 feat_v + b1) + b2) + b3 with the BF16 weights and
+ * FP32 accumulation.  feat: device n x 12; out: device n floats. */
+s3_status s3_mlp_forward(s3_mlp_t m, const float *feat, int64_t n, float *out, void *stream);
+
+/*
+ * Loss L = (1/n) sum_v (out_v - target_v)^2 over the n given nodes (forward with
+ * the BF16 weights) and its gradient with respect to the weights (FP32,
+ * accumulated per block and summed in a fixed order), kept in the model for
+ * s3_mlp_adam_step.  feat: device n x 12; target: device n.  loss (host,
+ * double) and grad (host, S3_MLP_PARAMS floats) are optional; when given the
+ * call synchronises `stream`.
+ */
+s3_status s3_mlp_loss_grad(s3_mlp_t m, const float *feat, const float *target, int64_t n, double *loss,
+                           float *grad, void *stream);
+
+/* One Adam step (bias-corrected) on the FP32 master weights with the last gradient;
+ * refreshes the BF16 copies. */
+s3_status s3_mlp_adam_step(s3_mlp_t m, float lr, float beta1, float beta2, float eps, void *stream);
+
+/*
+ * Warm start for s3_hcentrality: x0 = exp(MLP(features)) normalised to 1-norm 1.
+ * x0: device, n doubles, written.  Synchronises `stream` once (to shift the
+ * exponent by the largest prediction).
+ */
+s3_status s3_warmstart(s3_graph_t g, s3_mlp_t m, double *x0, void *stream);
+
+/* Training target of the warm start: target_v = log x_v - (1/n) sum_u log x_u for a positive
+ * centrality x (device, n doubles); target: device, n floats. */
+s3_status s3_mlp_target(s3_graph_t g, const double *x, float *target, void *stream);
+
+s3_status s3_mlp_destroy(s3_mlp_t m);
+
 /* ----------------------------------------------- allocation-free call --- */
 
 /* Largest node count s3_sttsvc_f32_noalloc accepts (its fixed scratch: 4 bytes per node). */

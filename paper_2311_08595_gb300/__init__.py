@@ -28,7 +28,8 @@ __all__ = [
     "s3_sttsvc", "s3_sttsvc_layout", "s3_sttsvc_host", "s3_sttsvc_profile", "s3_range_events", "s3_hcentrality",
     "s3_nqz_options_init", "s3_sttsvc_f32_noalloc", "s3_destroy", "s3_version", "lib_path",
     "Batch", "s3_batch_options_init", "s3_batch_create", "s3_sttsvc_batched", "s3_batch_autotune",
-    "s3_batch_destroy",
+    "s3_batch_destroy", "MLP", "s3_features", "s3_mlp_create", "s3_mlp_get_params", "s3_mlp_forward",
+    "s3_mlp_loss_grad", "s3_mlp_adam_step", "s3_warmstart", "s3_mlp_target", "s3_mlp_destroy",
 ]
 
 
@@ -287,6 +288,97 @@ def s3_batch_destroy(b):
     if b is not None and getattr(b, "handle", None):
         h, b.handle = b.handle, None
         check(load().s3_batch_destroy(h))
+
+
+class MLP:
+    """Owns an s3_mlp_t (warm-start network); released by s3_mlp_destroy."""
+
+    def __init__(self, handle):
+        self.handle = handle
+
+    def __del__(self):
+        try:
+            s3_mlp_destroy(self)
+        except Exception:
+            pass
+
+
+def s3_features(g, feat=None, stream=None):
+    """Per-node features (n x 12 float32 CUDA tensor)."""
+    import torch
+    if feat is None:
+        feat = torch.empty((g.n, _lib.S3_MLP_FEATURES), dtype=torch.float32, device="cuda")
+    if not feat.is_cuda or not feat.is_contiguous() or feat.numel() != g.n * _lib.S3_MLP_FEATURES:
+        raise ValueError("feat must be a contiguous CUDA tensor of n x 12 floats")
+    check(load().s3_features(g.handle, ptr(feat), _stream(stream)))
+    return feat
+
+
+def s3_mlp_create(params=None, seed=0):
+    p = None
+    if params is not None:
+        params = np.ascontiguousarray(params, dtype=np.float32)
+        if params.size != _lib.S3_MLP_PARAMS:
+            raise ValueError(f"need {_lib.S3_MLP_PARAMS} parameters")
+        p = params.ctypes.data
+    h = ctypes.c_void_p()
+    check(load().s3_mlp_create(p, int(seed), ctypes.byref(h)))
+    m = MLP(h)
+    m._keep = params
+    return m
+
+
+def s3_mlp_get_params(m, bf16=False):
+    out = np.empty(_lib.S3_MLP_PARAMS, dtype=np.float32)
+    check(load().s3_mlp_get_params(m.handle, out.ctypes.data, int(bool(bf16))))
+    return out
+
+
+def s3_mlp_forward(m, feat, out=None, stream=None):
+    import torch
+    n = feat.shape[0]
+    if out is None:
+        out = torch.empty(n, dtype=torch.float32, device=feat.device)
+    check(load().s3_mlp_forward(m.handle, ptr(feat), int(n), ptr(out), _stream(stream)))
+    return out
+
+
+def s3_mlp_loss_grad(m, feat, target, want_grad=True, stream=None):
+    """Loss and (optionally) its gradient as a numpy array; the gradient stays in m for the Adam step."""
+    n = feat.shape[0]
+    loss = ctypes.c_double()
+    grad = np.empty(_lib.S3_MLP_PARAMS, dtype=np.float32) if want_grad else None
+    check(load().s3_mlp_loss_grad(m.handle, ptr(feat), ptr(target), int(n), ctypes.byref(loss),
+                                  None if grad is None else grad.ctypes.data, _stream(stream)))
+    return float(loss.value), grad
+
+
+def s3_mlp_adam_step(m, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8, stream=None):
+    check(load().s3_mlp_adam_step(m.handle, float(lr), float(beta1), float(beta2), float(eps), _stream(stream)))
+
+
+def s3_warmstart(g, m, x0=None, stream=None):
+    import torch
+    if x0 is None:
+        x0 = torch.empty(g.n, dtype=torch.float64, device="cuda")
+    _check_vec(g, x0, "x0")
+    check(load().s3_warmstart(g.handle, m.handle, ptr(x0), _stream(stream)))
+    return x0
+
+
+def s3_mlp_target(g, x, target=None, stream=None):
+    import torch
+    if target is None:
+        target = torch.empty(g.n, dtype=torch.float32, device="cuda")
+    _check_vec(g, x, "x")
+    check(load().s3_mlp_target(g.handle, ptr(x), ptr(target), _stream(stream)))
+    return target
+
+
+def s3_mlp_destroy(m):
+    if m is not None and getattr(m, "handle", None):
+        h, m.handle = m.handle, None
+        check(load().s3_mlp_destroy(h))
 
 
 def s3_destroy(g):

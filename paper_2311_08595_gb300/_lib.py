@@ -16,6 +16,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libs3ttvc.so")
 
 S3_MAX_RANK = 128
+S3_MLP_FEATURES, S3_MLP_HIDDEN, S3_MLP_PARAMS = 12, 64, 5057
 S3_OK, S3_EINVAL, S3_ENOMEM, S3_ECUDA, S3_ENOCONV, S3_ETIMEOUT, S3_ERANGE, S3_ENOTSUP = range(8)
 S3_F32, S3_F64 = 0, 1
 S3_REDUCE_SEGMENTED, S3_REDUCE_ATOMIC = 0, 1
@@ -103,6 +104,15 @@ SIGNATURES = {
     "s3_sttsvc_batched": (_I32, [_P, _I32, _P, _P, _P]),
     "s3_batch_autotune": (_I32, [_P, _I32, _P, _P, ctypes.POINTER(s3_tune_result), _P]),
     "s3_batch_destroy": (_I32, [_P]),
+    "s3_features": (_I32, [_P, _P, _P]),
+    "s3_mlp_create": (_I32, [_P, ctypes.c_uint64, ctypes.POINTER(_P)]),
+    "s3_mlp_get_params": (_I32, [_P, _P, _I32]),
+    "s3_mlp_forward": (_I32, [_P, _P, _I64, _P, _P]),
+    "s3_mlp_loss_grad": (_I32, [_P, _P, _P, _I64, ctypes.POINTER(ctypes.c_double), _P, _P]),
+    "s3_mlp_adam_step": (_I32, [_P, ctypes.c_float, ctypes.c_float, ctypes.c_float, ctypes.c_float, _P]),
+    "s3_warmstart": (_I32, [_P, _P, _P, _P]),
+    "s3_mlp_target": (_I32, [_P, _P, _P, _P]),
+    "s3_mlp_destroy": (_I32, [_P]),
     "s3_destroy": (_I32, [_P]),
     "s3_last_error": (ctypes.c_char_p, []),
     "s3_status_string": (ctypes.c_char_p, [_I32]),

@@ -62,6 +62,8 @@ struct s3_graph_s {
     int32_t hist_cap = 0;
 
     int32_t last_launches = 0;       // kernels launched by the last S^3TTVc call
+    uint32_t *d_feat_scratch = nullptr;  // warm-start feature counters (48 bytes per node)
+    float *d_ws = nullptr;               // warm-start features, predictions, partials
     // concurrent buckets: forked streams and events, bucket order (heaviest first) and cost
     int n_streams = 1;
     cudaStream_t aux[8] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
