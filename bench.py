@@ -317,6 +317,8 @@ def run_gpu(args):
     if rank == 0 and ws == 1 and (args.batched or not args.skip_extras):
         out["batched"] = batched(dev, scale=args.batched_scale)
     if rank == 0 and ws == 1 and not args.skip_extras:
+        out["large_rank"] = large_rank(dev)
+        out["layouts"] = layouts(dev)
         out["centrality"] = centrality(hg, dev)
         rate, cores, sample = time_oracle(hg, x_np)
         out["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample}
@@ -402,6 +404,90 @@ def warm_start(lcc, dev, graphs=48, n=50000, epochs=20):
         out[name] = ws.evaluate(lcc, model, tol=1e-8, precision=prec)
     out.update({"train_graphs": graphs, "train_n": n, "train_nodes": int(feat.shape[0]), "epochs": epochs,
                 "loss_first": hist[0][1], "loss_last": hist[-1][1], "data_s": t_data, "train_s": t_train})
+    return out
+
+
+def _time_calls(g, x, y, reps):
+    import torch
+
+    import paper_2311_08595_gb300 as s3
+    s3.s3_sttsvc(g, x, y)
+    torch.cuda.synchronize()
+    st = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(st)
+    for _ in range(reps):
+        s3.s3_sttsvc(g, x, y)
+    e1.record(st)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / reps
+
+
+def large_rank(dev, sample=300):
+    """Rank-100 stress workload: n=200k, m=1M, Geometric(0.1) sizes on {2..100}, x ~ U(0.5,1.5).
+    FP32 and FP64 throughput; FP32 error per node against the GPU FP64 result, and the FP64
+    result against the CPU oracle on sampled nodes."""
+    import torch
+
+    import oracle
+    import paper_2311_08595_gb300 as s3
+    import s3synth
+    hg = s3synth.config_large_rank()
+    x_np = s3synth.x_uniform(hg.n, 0.5, 1.5, 3)
+    g = s3.s3_build_format(hg.n, hg.edge_ptr, hg.members)
+    x64 = torch.tensor(x_np, dtype=torch.float64, device=dev)
+    x32 = x64.float()
+    y64, y32 = torch.empty_like(x64), torch.empty_like(x32)
+    ms32 = _time_calls(g, x32, y32, 3)
+    ms64 = _time_calls(g, x64, y64, 2)
+    a, b = y32.double().cpu().numpy(), y64.cpu().numpy()
+    d = hg.degrees()
+    rel = np.abs(a - b)[d > 0] / np.abs(b)[d > 0]
+    nodes = np.random.default_rng(0).choice(np.nonzero(d > 0)[0], size=sample, replace=False)
+    want = oracle.ttsv1(hg, x_np, nodes=nodes, nthreads=oracle.max_threads())
+    e64 = float(np.max(np.abs(b[nodes] - want) / np.abs(want)))
+    s3.s3_destroy(g)
+    return {"workload": "largerank n=200k m=1M geometric(0.1) sizes on 2..100, x~U(0.5,1.5)", "nnz": hg.nnz,
+            "fp32_ms": ms32, "fp64_ms": ms64, "fp32_members_per_s": hg.nnz / (ms32 * 1e-3),
+            "fp64_members_per_s": hg.nnz / (ms64 * 1e-3), "fp32_speedup": ms64 / ms32,
+            "fp32_rel_err_per_node": {"max": float(rel.max()), "median": float(np.median(rel)),
+                                      "p99": float(np.quantile(rel, 0.99))},
+            "fp64_vs_oracle_max_rel_err": e64, "oracle_sample_nodes": sample}
+
+
+def layouts(dev):
+    """Edge layout (per-edge prefix/suffix products) vs the level-by-level CCSS forest, FP32, on a
+    power-law graph (n=100k, m=500k, rank 25) and on nested edge families (Fig. 3)."""
+    import torch
+
+    import paper_2311_08595_gb300 as s3
+    import s3synth
+    out = {}
+    cases = {"powerlaw_n100k": s3synth.config_powerlaw(n=100000, m=500000, seed=8),
+             "nested_4000x6": s3synth.nested(chains=4000, length=6, start=5, step=5, n=200000)}
+    for name, hg in cases.items():
+        g = s3.s3_build_format(hg.n, hg.edge_ptr, hg.members, build_ccss=1)
+        info = s3.s3_graph_query(g)
+        x = torch.tensor(s3synth.x_uniform(hg.n, 0.5, 1.5, 1), dtype=torch.float32, device=dev)
+        ye, yc = torch.empty_like(x), torch.empty_like(x)
+        ms_e = _time_calls(g, x, ye, 5)
+        s3.s3_sttsvc_layout(g, s3.S3_LAYOUT_CCSS, x, yc)
+        torch.cuda.synchronize()
+        st = torch.cuda.current_stream()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        for _ in range(5):
+            s3.s3_sttsvc_layout(g, s3.S3_LAYOUT_CCSS, x, yc)
+        e1.record(st)
+        torch.cuda.synchronize()
+        ms_c = e0.elapsed_time(e1) / 5
+        sizes = np.bincount(hg.sizes(), minlength=hg.rank + 1)
+        edge_products = int(sum(c * max(2 * s - 5, 0) for s, c in enumerate(sizes)))
+        diff = float(((yc - ye).abs() / ye.abs().clamp_min(1e-30)).max())
+        out[name] = {"nnz": hg.nnz, "edge_ms": ms_e, "ccss_ms": ms_c, "ccss_forest_nodes": info["ccss_nodes"],
+                     "ccss_products": info["ccss_products"], "edge_layout_products": edge_products,
+                     "max_rel_diff": diff}
+        s3.s3_destroy(g)
     return out
 
 

@@ -1,7 +1,7 @@
 """FP64 oracle of the learned warm start -- test infrastructure only.
 
-Restates, in plain numpy, the warm-start network the library documents
-(include/s3ttvc.h): per-node features, the 12-64-64-1 ReLU MLP evaluated with
+Restates, in plain numpy, the warm-start network as its C interface documents
+it: per-node features, the 12-64-64-1 ReLU MLP evaluated with
 BF16-rounded weights, the mean-squared loss, its gradient, and one Adam step.
 The gradient is pinned by central finite differences of the loss
 (tests/test_oracle_mlp.py), the features by a direct loop over the edges.

@@ -185,7 +185,7 @@ s3_status build_host_format(int64_t n, int64_t m, const int64_t *edge_ptr, const
         int64_t d = f.inc_ptr[v + 1] - f.inc_ptr[v];
         if (d <= kSmallDeg)
             f.red_small.push_back((int32_t)v);
-        else if (d <= kPiece)
+        else if (d <= kMedDeg)
             f.red_med.push_back((int32_t)v);
         else {
             f.big_node.push_back((int32_t)v);

@@ -61,8 +61,8 @@ struct HostFormat {
     std::vector<int64_t> inc_ptr;         // n+1: node v owns incidence slots [inc_ptr[v], inc_ptr[v+1])
     // deterministic reduce work lists
     std::vector<int32_t> red_small;       // nodes with degree <= kSmallDeg (thread per node)
-    std::vector<int32_t> red_med;         // kSmallDeg < degree <= kPiece (warp per node)
-    std::vector<int32_t> big_node;        // degree > kPiece
+    std::vector<int32_t> red_med;         // kSmallDeg < degree <= kMedDeg (warp per node)
+    std::vector<int32_t> big_node;        // degree > kMedDeg (pieces of at most kPiece slots)
     std::vector<int32_t> big_piece_ptr;   // pieces of big_node[k]: [big_piece_ptr[k], big_piece_ptr[k+1])
     std::vector<int64_t> piece_start;     // first incidence slot of each piece
     std::vector<int32_t> piece_len;
@@ -71,6 +71,7 @@ struct HostFormat {
 };
 
 constexpr int kSmallDeg = 32;
+constexpr int kMedDeg = 4096;
 constexpr int kPiece = 4096;
 
 s3_status build_host_format(int64_t n, int64_t m, const int64_t *edge_ptr, const int32_t *members,

@@ -50,7 +50,7 @@ struct ReduceArgs {
     const int64_t *inc_ptr;        // n+1
     const int32_t *small_nodes;    // degree <= kSmallDeg
     int64_t n_small;
-    const int32_t *med_nodes;      // kSmallDeg < degree <= kPiece
+    const int32_t *med_nodes;      // kSmallDeg < degree <= kMedDeg
     int64_t n_med;
     const int64_t *piece_start;    // pieces of big nodes
     const int32_t *piece_len;

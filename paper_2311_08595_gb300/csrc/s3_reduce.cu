@@ -5,7 +5,7 @@
 //   degree <= 32          one thread per node,
 //   degree <= 4096        one warp per node,
 //   larger                pieces of 4096 slots, one block each, then one
-//                         thread per node adds its pieces in order.
+//                         warp per node adds its pieces in a fixed order.
 // Every thread/warp/block adds in a fixed order, so the result does not
 // depend on scheduling.  FP32 sums carry a two-sum compensation term.
 #include <cuda_runtime.h>
@@ -110,7 +110,15 @@ __global__ void __launch_bounds__(kRedThreads) reduce_kernel(ReduceArgs r, const
         int v = r.med_nodes[i];
         int64_t b = r.inc_ptr[v], t = r.inc_ptr[v + 1];
         A a;
-        for (int64_t k = b + lane; k < t; k += 32) a.add(buf[k]);
+        int64_t k = b + lane;
+        for (; k + 96 < t; k += 128) {  // four loads in flight per lane, added in order
+            T v0 = buf[k], v1 = buf[k + 32], v2 = buf[k + 64], v3 = buf[k + 96];
+            a.add(v0);
+            a.add(v1);
+            a.add(v2);
+            a.add(v3);
+        }
+        for (; k < t; k += 32) a.add(buf[k]);
         a = warp_reduce(a);
         if (lane == 0) y[v] = (T)a.value();
     } else {
@@ -119,7 +127,16 @@ __global__ void __launch_bounds__(kRedThreads) reduce_kernel(ReduceArgs r, const
         int64_t b = r.piece_start[pc];
         int len = r.piece_len[pc];
         A a;
-        for (int k = tid; k < len; k += kRedThreads) a.add(buf[b + k]);
+        int k = tid;
+        for (; k + 3 * kRedThreads < len; k += 4 * kRedThreads) {
+            T v0 = buf[b + k], v1 = buf[b + k + kRedThreads], v2 = buf[b + k + 2 * kRedThreads],
+              v3 = buf[b + k + 3 * kRedThreads];
+            a.add(v0);
+            a.add(v1);
+            a.add(v2);
+            a.add(v3);
+        }
+        for (; k < len; k += kRedThreads) a.add(buf[b + k]);
         a = warp_reduce(a);
         if ((tid & 31) == 0) part[tid >> 5] = a;
         __syncthreads();
@@ -131,15 +148,18 @@ __global__ void __launch_bounds__(kRedThreads) reduce_kernel(ReduceArgs r, const
     }
 }
 
+// one warp per big node: lane l adds pieces l, l+32, ... in order, then a fixed shuffle tree
 template <typename T>
 __global__ void finalize_big_kernel(ReduceArgs r, T *__restrict__ y) {
     if (r.skip && *r.skip) return;
     using A = typename AccOf<T>::type;
-    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
     if (i >= r.n_big) return;
     A a;
-    for (int p = r.big_piece_ptr[i]; p < r.big_piece_ptr[i + 1]; ++p) load_partial(r.partial, p, a);
-    y[r.big_nodes[i]] = (T)a.value();
+    for (int p = r.big_piece_ptr[i] + lane; p < r.big_piece_ptr[i + 1]; p += 32) load_partial(r.partial, p, a);
+    a = warp_reduce(a);
+    if (lane == 0) y[r.big_nodes[i]] = (T)a.value();
 }
 
 template <typename T>
@@ -153,7 +173,7 @@ cudaError_t launch_reduce_t(const ReduceArgs &r, const T *buf, T *y, cudaStream_
         if (e != cudaSuccess) return e;
     }
     if (r.n_big > 0) {
-        finalize_big_kernel<T><<<(unsigned)((r.n_big + 127) / 128), 128, 0, st>>>(r, y);
+        finalize_big_kernel<T><<<(unsigned)((r.n_big * 32 + 127) / 128), 128, 0, st>>>(r, y);
         return cudaGetLastError();
     }
     return cudaSuccess;

@@ -172,6 +172,37 @@ __device__ __forceinline__ void toeplitz_inplace(T (&P)[W], const T (&a)[W]) {
     }
 }
 
+// xk[k] = x/(k+1), k = 0..W-1: the ratios of consecutive coefficients of Ebar(x)
+template <typename T, int W>
+__device__ __forceinline__ void ratio_table(T X, T (&xk)[W]) {
+#pragma unroll
+    for (int k = 0; k < W; ++k) xk[k] = X * (T(1) / T(k + 1));
+}
+
+// P <- P * Ebar(x) on the window, in Horner form: with xk[k] = x/(k+1),
+//   P_new[j] = x (P[j] + x/2 (P[j-1] + x/3 (P[j-2] + ... + x/(j+1) P[0])))
+// (j + 1 multiply-adds per coefficient, no power table).  Top-down, in place.
+template <typename T, int W>
+__device__ __forceinline__ void toeplitz_horner(T (&P)[W], const T (&xk)[W]) {
+#pragma unroll
+    for (int j = W - 1; j >= 0; --j) {
+        T acc = P[0];
+#pragma unroll
+        for (int r = 1; r <= j; ++r) acc = Arith<T>::fma_(xk[j - r + 1], acc, P[r]);
+        P[j] = xk[0] * acc;
+    }
+}
+
+// [t^top] of Q * Ebar(x) where Q's window ends at degree top-1:
+//   sum_{k=1}^{W} x^k/k! Q[W-k] = x (Q[W-1] + x/2 (Q[W-2] + ... + x/W Q[0]))
+template <typename T, int W>
+__device__ __forceinline__ T top_horner(const T (&Q)[W], const T (&xk)[W]) {
+    T acc = Q[0];
+#pragma unroll
+    for (int r = 1; r < W; ++r) acc = Arith<T>::fma_(xk[W - r], acc, Q[r]);
+    return xk[0] * acc;
+}
+
 // ---------------------------------------------------------- cp.async ---
 
 __device__ __forceinline__ unsigned smem_addr(const void *p) { return (unsigned)__cvta_generic_to_shared(p); }
@@ -185,67 +216,97 @@ __device__ __forceinline__ void cp_async(void *smem_dst, const void *gmem_src) {
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
 
+// Final scaling of one result: c = val * K * 2^(-p(N-1)) [* 2^(-(N-1) e_v) in biased mode]
+// as one or two exact power-of-two multiplies (ldexp only when an exponent leaves the
+// normal range).
 template <typename T>
+__device__ __forceinline__ T scale_result(T val, const EdgeBucketArgs &b, int p, int bias_e,
+                                          unsigned long long *range_events);
+
+template <>
+__device__ __forceinline__ float scale_result<float>(float val, const EdgeBucketArgs &b, int p, int bias_e,
+                                                     unsigned long long *range_events) {
+    const int ex = b.Ke - (p + bias_e) * (b.N - 1);
+    float c = (unsigned)(ex + 126) <= 253u ? (val * b.Km) * Arith<float>::pow2(ex) : ldexpf(val * b.Km, ex);
+    // zero, subnormal or non-finite result of a positive value: exponent field 0 or 255
+    const unsigned ef = (__float_as_uint(c) >> 23) & 0xffu;
+    if ((ef == 0u || ef == 0xffu) && val > 0.f && range_events) atomicAdd(range_events, 1ull);
+    return c;
+}
+
+template <>
+__device__ __forceinline__ double scale_result<double>(double val, const EdgeBucketArgs &b, int p, int bias_e,
+                                                       unsigned long long *range_events) {
+    const int ex = -(p + bias_e) * (b.N - 1);
+    double c = (unsigned)(ex + 1022) <= 2045u ? (val * b.K) * Arith<double>::pow2(ex) : ldexp(val * b.K, ex);
+    const unsigned ef = (unsigned)((__double_as_longlong(c) >> 52) & 0x7ff);
+    if ((ef == 0u || ef == 0x7ffu) && val > 0.0 && range_events) atomicAdd(range_events, 1ull);
+    return c;
+}
+
+// BUF: results go to the node-sorted buffer at slot sl; otherwise atomically to y[v].
+template <typename T, bool BUF>
 __device__ __forceinline__ void emit_value(const EdgeBucketArgs &b, const EdgeOutArgs &o, int v, int sl, T val,
                                            int p, T xhat) {
     int bias_e = o.bias ? (Arith<T>::expo(xhat) - p) : 0;
-    T c = finalize_value<T>(val, b, p, bias_e, o.range_events);
-    if (o.mode == kOutBuffer) {
+    T c = scale_result<T>(val, b, p, bias_e, o.range_events);
+    if constexpr (BUF) {
         reinterpret_cast<T *>(o.out)[sl] = c;
     } else {
         scatter_atomic<T>(o, v, c);
     }
 }
 
-// All contributions of one edge.  Xs[i*BS]: the member values (overwritten by
-// their scaled copies); Pre: this thread's column for Pre_2..Pre_{s-1};
-// ib/sb: this thread's member ids / incidence slots (stride BS).
-template <typename T, int W>
-__device__ __forceinline__ void edge_compute(const EdgeBucketArgs &b, const EdgeOutArgs &o, T *Xs, T *Pre,
+// All contributions of one edge.  Xs[i*BS]: the member values; Pre: this
+// thread's column for Pre_2..Pre_{s-1}; ib/sb: this thread's member ids /
+// incidence slots (stride BS).
+template <typename T, int W, bool BUF>
+__device__ __forceinline__ void edge_compute(const EdgeBucketArgs &b, const EdgeOutArgs &o, const T *Xs, T *Pre,
                                              const int32_t *ib, const int32_t *sb, int BS, int s) {
     T S = T(0);
     for (int i = 0; i < s; ++i) S += Arith<T>::absv(Xs[i * BS]);
     const int p = scale_exponent<T>(S, b.target);
     const T g = Arith<T>::pow2(p);
-    for (int i = 0; i < s; ++i) Xs[i * BS] *= g;
-    const bool buf = o.mode == kOutBuffer;
+    const int32_t *ob = BUF ? sb : ib;  // where each member's result goes
 
     // forward: P = Pre_2, then Pre_3 .. Pre_s (windows Pre_2..Pre_{s-1} kept in shared memory)
     T P[W];
-    power_table<T, W>(Xs[0], P);
+    power_table<T, W>(Xs[0] * g, P);
     for (int i = 1; i <= s - 2; ++i) {
 #pragma unroll
         for (int j = 0; j < W; ++j) Pre[((i - 1) * W + j) * BS] = P[j];
-        T a[W];
-        power_table<T, W>(Xs[i * BS], a);
-        toeplitz_inplace<T, W>(P, a);
+        T xk[W];
+        ratio_table<T, W>(Xs[i * BS] * g, xk);
+        toeplitz_horner<T, W>(P, xk);
     }
     // P = Pre_s.  backward: Q = Suf_{s-1} = Ebar(x_{v_s})
     T Q[W];
-    power_table<T, W>(Xs[(s - 1) * BS], Q);
+    const T xs_last = Xs[(s - 1) * BS] * g;
+    power_table<T, W>(xs_last, Q);
     T F = T(0);
 #pragma unroll
     for (int j = 0; j <= W - 2; ++j) F = Arith<T>::fma_(P[j], Q[W - 2 - j], F);
-    emit_value<T>(b, o, buf ? 0 : ib[(s - 1) * BS], buf ? sb[(s - 1) * BS] : 0, F + P[W - 1], p,
-                  Xs[(s - 1) * BS]);
+    {
+        const int t = ob[(s - 1) * BS];
+        emit_value<T, BUF>(b, o, t, t, F + P[W - 1], p, xs_last);
+    }
     T top = T(0);
     for (int q = s - 2; q >= 1; --q) {
         // Q = Suf_{q+1}; Pre_{q+1} sits in slot q-1
         T D = T(0);
 #pragma unroll
         for (int j = 0; j < W; ++j) D = Arith<T>::fma_(Pre[((q - 1) * W + j) * BS], Q[W - 1 - j], D);
-        emit_value<T>(b, o, buf ? 0 : ib[q * BS], buf ? sb[q * BS] : 0, F + D, p, Xs[q * BS]);
-        T a[W];
-        power_table<T, W>(Xs[q * BS], a);
-        if (q >= 2) {
-            toeplitz_inplace<T, W>(Q, a);
-        } else {
-#pragma unroll
-            for (int jp = 0; jp < W; ++jp) top = Arith<T>::fma_(a[W - 1 - jp], Q[jp], top);
-        }
+        const T xq = Xs[q * BS] * g;
+        const int t = ob[q * BS];
+        emit_value<T, BUF>(b, o, t, t, F + D, p, xq);
+        T xk[W];
+        ratio_table<T, W>(xq, xk);
+        if (q >= 2) toeplitz_horner<T, W>(Q, xk);
+        else top = top_horner<T, W>(Q, xk);
     }
     T D1 = (s == 2) ? Q[W - 1] : top;
-    emit_value<T>(b, o, buf ? 0 : ib[0], buf ? sb[0] : 0, F + D1, p, Xs[0]);
+    const int t0 = ob[0];
+    emit_value<T, BUF>(b, o, t0, t0, F + D1, p, Xs[0] * g);
 }
 
 // Shared memory per thread, interleaved across the block (element k of thread t
@@ -258,8 +319,9 @@ __host__ __device__ constexpr size_t thread_smem_words(int s, int W) {
 
 // One thread per edge, several edges per thread (grid-stride), software
 // pipelined with cp.async: while edge k is computed, the x gathers of edge k+1
-// and the id/slot loads of edge k+2 are in flight.
-template <typename T, int W>
+// and the id/slot loads of edge k+2 are in flight.  Ring buffers rotate by
+// pointer; global addresses advance by the grid stride.
+template <typename T, int W, bool BUF>
 __global__ void __launch_bounds__(256) edge_thread_kernel(EdgeBucketArgs b, const T *__restrict__ x,
                                                           EdgeOutArgs o) {
     if (o.skip && *o.skip) return;
@@ -268,44 +330,55 @@ __global__ void __launch_bounds__(256) edge_thread_kernel(EdgeBucketArgs b, cons
     const int tid = threadIdx.x;
     const int s = b.s;
     T *tb = reinterpret_cast<T *>(smem_raw);
-    T *Xb0 = tb + tid;
-    T *Xb1 = tb + (size_t)s * BS + tid;
+    T *xc = tb + tid;                     // X of the edge being computed
+    T *xn = tb + (size_t)s * BS + tid;    // X of the next edge (in flight)
     T *Pre = tb + (size_t)2 * s * BS + tid;
     int32_t *ibase = reinterpret_cast<int32_t *>(tb + (size_t)(2 * s + (s > 2 ? (s - 2) * W : 0)) * BS) + tid;
-    const bool need_slot = o.mode == kOutBuffer;
+    const size_t ring = (size_t)s * BS;
+    // ring slots (ids; the slots array sits 3 rings further): current, next, after next
+    int32_t *r0 = ibase, *r1 = ibase + ring, *r2 = ibase + 2 * ring;
     const int64_t stride = (int64_t)gridDim.x * BS;
     int64_t e = (int64_t)blockIdx.x * BS + tid;
     if (e >= b.m) return;
+    const int64_t ld = b.ld;
+    const int32_t *gid = b.ids + e;       // member 0 of edge e; member i at gid + i*ld
+    const int32_t *gsl = b.slot + e;
 
-    auto ids_of = [&](int r) { return ibase + (size_t)r * s * BS; };
-    auto slots_of = [&](int r) { return ibase + (size_t)(3 + r) * s * BS; };
-    auto issue_ids = [&](int64_t ee, int r) {
-        int32_t *ib = ids_of(r), *sb = slots_of(r);
+    auto issue_ids = [&](const int32_t *gi, const int32_t *gs, int32_t *dst) {
+        int32_t *d = dst;
         for (int i = 0; i < s; ++i) {
-            cp_async<4>(ib + (size_t)i * BS, b.ids + (int64_t)i * b.ld + ee);
-            if (need_slot) cp_async<4>(sb + (size_t)i * BS, b.slot + (int64_t)i * b.ld + ee);
+            cp_async<4>(d, gi);
+            if (BUF) cp_async<4>(d + 3 * ring, gs);
+            d += BS;
+            gi += ld;
+            gs += ld;
         }
     };
-    auto issue_x = [&](int r, T *xb) {
-        const int32_t *ib = ids_of(r);
-        for (int i = 0; i < s; ++i) cp_async<(int)sizeof(T)>(xb + (size_t)i * BS, x + ib[(size_t)i * BS]);
+    auto issue_x = [&](const int32_t *src, T *xb) {
+        for (int i = 0; i < s; ++i) cp_async<(int)sizeof(T)>(xb + (size_t)i * BS, x + src[(size_t)i * BS]);
     };
 
-    issue_ids(e, 0);
+    issue_ids(gid, gsl, r0);
     cp_async_commit();
     cp_async_wait_all();
-    issue_x(0, Xb0);
-    if (e + stride < b.m) issue_ids(e + stride, 1);
+    issue_x(r0, xc);
+    if (e + stride < b.m) issue_ids(gid + stride, gsl + stride, r1);
     cp_async_commit();
-    for (int k = 0; e < b.m; e += stride, ++k) {
-        const int rc = k % 3;
-        T *xc = (k & 1) ? Xb1 : Xb0;
-        T *xn = (k & 1) ? Xb0 : Xb1;
+    for (; e < b.m; e += stride) {
         cp_async_wait_all();
-        if (e + stride < b.m) issue_x((k + 1) % 3, xn);
-        if (e + 2 * stride < b.m) issue_ids(e + 2 * stride, (k + 2) % 3);
+        if (e + stride < b.m) issue_x(r1, xn);
+        if (e + 2 * stride < b.m) issue_ids(gid + 2 * stride, gsl + 2 * stride, r2);
         cp_async_commit();
-        edge_compute<T, W>(b, o, xc, Pre, ids_of(rc), slots_of(rc), BS, s);
+        edge_compute<T, W, BUF>(b, o, xc, Pre, r0, r0 + 3 * ring, BS, s);
+        gid += stride;
+        gsl += stride;
+        int32_t *t = r0;
+        r0 = r1;
+        r1 = r2;
+        r2 = t;
+        T *tx = xc;
+        xc = xn;
+        xn = tx;
     }
     cp_async_wait_all();
 }
@@ -492,8 +565,8 @@ constexpr size_t kSmemCap = 96 * 1024;        // per block, thread-per-edge kern
 constexpr size_t kSmemCapWarp = 200 * 1024;   // per block, warp-per-edge kernel
 constexpr int kMaxThreadW = 32;
 
-template <typename T, int W>
-cudaError_t launch_thread_w(const EdgeBucketArgs &b, const T *x, const EdgeOutArgs &o, int bs, cudaStream_t st) {
+template <typename T, int W, bool BUF>
+cudaError_t launch_thread_wb(const EdgeBucketArgs &b, const T *x, const EdgeOutArgs &o, int bs, cudaStream_t st) {
     size_t smem = thread_smem_words<T>(b.s, W) * 4 * (size_t)bs;
     // enough blocks to fill the GPU (several edges per thread beyond that)
     static int sms = 0;
@@ -504,7 +577,7 @@ cudaError_t launch_thread_w(const EdgeBucketArgs &b, const T *x, const EdgeOutAr
         if (sms <= 0) sms = 148;
     }
     int per_sm = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, edge_thread_kernel<T, W>, bs, smem) != cudaSuccess ||
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, edge_thread_kernel<T, W, BUF>, bs, smem) != cudaSuccess ||
         per_sm <= 0) {
         cudaGetLastError();
         per_sm = 1;
@@ -512,13 +585,23 @@ cudaError_t launch_thread_w(const EdgeBucketArgs &b, const T *x, const EdgeOutAr
     int64_t full = (int64_t)sms * per_sm;
     int64_t need = (b.m + bs - 1) / bs;
     int64_t grid = need < full ? need : full;
-    edge_thread_kernel<T, W><<<(unsigned)grid, bs, smem, st>>>(b, x, o);
+    edge_thread_kernel<T, W, BUF><<<(unsigned)grid, bs, smem, st>>>(b, x, o);
     return cudaGetLastError();
 }
 
 template <typename T, int W>
+cudaError_t launch_thread_w(const EdgeBucketArgs &b, const T *x, const EdgeOutArgs &o, int bs, cudaStream_t st) {
+    return o.mode == kOutBuffer ? launch_thread_wb<T, W, true>(b, x, o, bs, st)
+                                : launch_thread_wb<T, W, false>(b, x, o, bs, st);
+}
+
+template <typename T, int W>
 cudaError_t prepare_thread_w() {
-    return cudaFuncSetAttribute(edge_thread_kernel<T, W>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemCap);
+    cudaError_t e =
+        cudaFuncSetAttribute(edge_thread_kernel<T, W, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemCap);
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(edge_thread_kernel<T, W, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)kSmemCap);
 }
 
 #define S3_W_CASES(M) \
