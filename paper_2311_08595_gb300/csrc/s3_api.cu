@@ -130,20 +130,7 @@ s3_status run_edges(s3_graph_s *g, s3_dtype dt, const void *x, void *y, int bias
     }
     if (mid) S3_CUDA(cudaEventRecord(mid, st));
     if (seg) {
-        ReduceArgs r{};
-        r.inc_ptr = g->d_inc_ptr;
-        r.small_nodes = g->d_small;
-        r.n_small = g->n_small;
-        r.med_nodes = g->d_med;
-        r.n_med = g->n_med;
-        r.piece_start = g->d_piece_start;
-        r.piece_len = g->d_piece_len;
-        r.n_pieces = g->n_pieces;
-        r.big_nodes = g->d_big_nodes;
-        r.big_piece_ptr = g->d_big_piece_ptr;
-        r.n_big = g->n_big;
-        r.partial = g->d_partial;
-        r.skip = skip;
+        const ReduceArgs r = reduce_args(g, skip);
         cudaError_t e = dt == S3_F32 ? launch_reduce_f32(r, (const float *)g->d_buf, (float *)y, st)
                                      : launch_reduce_f64(r, (const double *)g->d_buf, (double *)y, st);
         if (e != cudaSuccess) return cuda_fail(e, "reduce launch");
@@ -248,18 +235,23 @@ s3_status s3_build_format(int64_t n, int64_t m, const int64_t *edge_ptr, const i
     if ((st = upload(g, &g->d_ids, f.ids)) != S3_OK) return bail(st);
     if ((st = upload(g, &g->d_slot, f.slot)) != S3_OK) return bail(st);
     if ((st = upload(g, &g->d_inc_ptr, f.inc_ptr)) != S3_OK) return bail(st);
-    if ((st = upload(g, &g->d_small, f.red_small)) != S3_OK) return bail(st);
-    if ((st = upload(g, &g->d_med, f.red_med)) != S3_OK) return bail(st);
+    if ((st = upload(g, &g->d_grp_off, f.grp_off)) != S3_OK) return bail(st);
+    if ((st = upload(g, &g->d_grp_node, f.grp_node)) != S3_OK) return bail(st);
+    if ((st = upload(g, &g->d_grp_deg, f.grp_deg)) != S3_OK) return bail(st);
+    if ((st = upload(g, &g->d_med, f.med_node)) != S3_OK) return bail(st);
+    if ((st = upload(g, &g->d_med_off, f.med_off)) != S3_OK) return bail(st);
+    if ((st = upload(g, &g->d_med_len, f.med_len)) != S3_OK) return bail(st);
     if ((st = upload(g, &g->d_big_nodes, f.big_node)) != S3_OK) return bail(st);
     if ((st = upload(g, &g->d_big_piece_ptr, f.big_piece_ptr)) != S3_OK) return bail(st);
     if ((st = upload(g, &g->d_piece_start, f.piece_start)) != S3_OK) return bail(st);
     if ((st = upload(g, &g->d_piece_len, f.piece_len)) != S3_OK) return bail(st);
-    g->n_small = (int64_t)f.red_small.size();
-    g->n_med = (int64_t)f.red_med.size();
+    g->n_grp = (int64_t)f.grp_off.size();
+    g->n_med = (int64_t)f.med_node.size();
     g->n_big = (int64_t)f.big_node.size();
     g->n_pieces = (int64_t)f.piece_start.size();
     double *dd = nullptr;
-    if ((st = dev_alloc(g, &dd, (size_t)f.nnz)) != S3_OK) return bail(st);
+    g->buf_len = f.buf_len;
+    if ((st = dev_alloc(g, &dd, (size_t)f.buf_len)) != S3_OK) return bail(st);
     g->d_buf = dd;
     if ((st = dev_alloc(g, &dd, (size_t)g->n_pieces)) != S3_OK) return bail(st);
     g->d_partial = dd;

@@ -39,16 +39,12 @@ struct BatchEdgeArgs {
     unsigned long long *range_events;
 };
 
-struct ReduceGraph {
-    const int64_t *inc_ptr;
-    const int32_t *small_nodes, *med_nodes, *big_nodes, *big_piece_ptr, *piece_len;
-    const int64_t *piece_start;
-    int64_t n_small, n_med, n_big, n_pieces;
-};
+// per-graph reduce tables (the partial and skip fields are unused here)
+using ReduceGraph = ReduceArgs;
 
 struct ReduceTile {
     int32_t graph;
-    int32_t kind;   // 0: 256 small nodes, 1: 8 medium nodes, 2: one hub piece
+    int32_t kind;   // 0: 8 groups of 32 small nodes, 1: 8 medium nodes, 2: one hub piece
     int64_t first;
 };
 

@@ -306,7 +306,7 @@ s3_status s3_batch_create(int32_t count, const s3_graph_t *graphs, int32_t nvec,
     for (int32_t gi = 0; gi < count; ++gi)
         for (int32_t v = 0; v < nvec; ++v) {
             bt->buf_off.push_back(bt->buf_elems);
-            bt->buf_elems += std::max<int64_t>(graphs[gi]->nnz, 1);
+            bt->buf_elems += std::max<int64_t>(graphs[gi]->buf_len, 1);
             bt->part_off.push_back(bt->part_elems);
             bt->part_elems += std::max<int64_t>(graphs[gi]->n_pieces, 1);
         }
@@ -337,22 +337,10 @@ s3_status s3_batch_create(int32_t count, const s3_graph_t *graphs, int32_t nvec,
     std::vector<FinalTile> finals;
     for (int32_t gi = 0; gi < count; ++gi) {
         s3_graph_s *g = graphs[gi];
-        ReduceGraph r{};
-        r.inc_ptr = g->d_inc_ptr;
-        r.small_nodes = g->d_small;
-        r.med_nodes = g->d_med;
-        r.big_nodes = g->d_big_nodes;
-        r.big_piece_ptr = g->d_big_piece_ptr;
-        r.piece_len = g->d_piece_len;
-        r.piece_start = g->d_piece_start;
-        r.n_small = g->n_small;
-        r.n_med = g->n_med;
-        r.n_big = g->n_big;
-        r.n_pieces = g->n_pieces;
-        rg[gi] = r;
+        rg[gi] = reduce_args(g, nullptr);
         for (int64_t f = 0; f < g->n_pieces; ++f) rtiles.push_back({gi, 2, f});
         for (int64_t f = 0; f < g->n_med; f += 8) rtiles.push_back({gi, 1, f});
-        for (int64_t f = 0; f < g->n_small; f += 256) rtiles.push_back({gi, 0, f});
+        for (int64_t f = 0; f < g->n_grp; f += 8) rtiles.push_back({gi, 0, f});
         for (int64_t k = 0; k < g->n_big; ++k) finals.push_back({gi, (int32_t)k});
     }
     if ((s = batch_alloc(bt, &p, sizeof(ReduceGraph) * rg.size())) != S3_OK) return bail(s);

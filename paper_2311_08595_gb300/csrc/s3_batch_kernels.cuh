@@ -208,28 +208,30 @@ __global__ void __launch_bounds__(256) batch_reduce_kernel(BatchReduceArgs a) {
             const T *buf = reinterpret_cast<const T *>(a.bufs[jv]);
             T *y = reinterpret_cast<T *>(a.ys[jv]);
             if (rt.kind == 0) {
-                int64_t i = rt.first + tid;
-                if (i < g.n_small) {
-                    int node = g.small_nodes[i];
-                    int64_t b = g.inc_ptr[node], e = g.inc_ptr[node + 1];
+                const int64_t gi = rt.first + (tid >> 5);
+                if (gi < g.n_grp) {
+                    const int lane = tid & 31;
+                    const int node = g.grp_node[gi * 32 + lane];
+                    const int d = g.grp_deg[gi * 32 + lane];
+                    const T *p = buf + g.grp_off[gi] + lane;
                     A acc;
-                    int64_t k = b;
-                    for (; k + 4 <= e; k += 4) {
-                        T v0 = buf[k], v1 = buf[k + 1], v2 = buf[k + 2], v3 = buf[k + 3];
+                    int k = 0;
+                    for (; k + 4 <= d; k += 4) {
+                        T v0 = p[32 * k], v1 = p[32 * k + 32], v2 = p[32 * k + 64], v3 = p[32 * k + 96];
                         acc.add(v0);
                         acc.add(v1);
                         acc.add(v2);
                         acc.add(v3);
                     }
-                    for (; k < e; ++k) acc.add(buf[k]);
-                    y[node] = (T)acc.value();
+                    for (; k < d; ++k) acc.add(p[32 * k]);
+                    if (node >= 0) y[node] = (T)acc.value();
                 }
             } else if (rt.kind == 1) {
                 int64_t i = rt.first + (tid >> 5);
                 if (i < g.n_med) {
                     const int lane = tid & 31;
-                    int node = g.med_nodes[i];
-                    int64_t b = g.inc_ptr[node], e = g.inc_ptr[node + 1];
+                    const int node = g.med_nodes[i];
+                    const int64_t b = g.med_off[i], e = b + g.med_len[i];
                     A acc;
                     int64_t k = b + lane;
                     for (; k + 96 < e; k += 128) {

@@ -243,20 +243,7 @@ s3_status run_ccss_t(s3_graph_s *g, const T *x, T *y, int bias, const int32_t *s
         if (e != cudaSuccess) return cuda_fail(e, "single-member launch");
     }
     if (seg) {
-        ReduceArgs r{};
-        r.inc_ptr = g->d_inc_ptr;
-        r.small_nodes = g->d_small;
-        r.n_small = g->n_small;
-        r.med_nodes = g->d_med;
-        r.n_med = g->n_med;
-        r.piece_start = g->d_piece_start;
-        r.piece_len = g->d_piece_len;
-        r.n_pieces = g->n_pieces;
-        r.big_nodes = g->d_big_nodes;
-        r.big_piece_ptr = g->d_big_piece_ptr;
-        r.n_big = g->n_big;
-        r.partial = g->d_partial;
-        r.skip = skip;
+        const ReduceArgs r = reduce_args(g, skip);
         cudaError_t e = sizeof(T) == 4 ? launch_reduce_f32(r, (const float *)g->d_buf, (float *)y, st)
                                        : launch_reduce_f64(r, (const double *)g->d_buf, (double *)y, st);
         if (e != cudaSuccess) return cuda_fail(e, "reduce launch");

@@ -163,40 +163,84 @@ s3_status build_host_format(int64_t n, int64_t m, const int64_t *edge_ptr, const
         }
     }
 
-    // node-sorted incidence: slots ordered by node, then bucket, then edge, then member
+    // degrees (inc_ptr holds their prefix sums)
     f.inc_ptr.assign(n + 1, 0);
     for (int64_t j = 0; j < nnz; ++j) f.inc_ptr[members[j] + 1]++;
     for (int64_t v = 0; v < n; ++v) {
         f.max_degree = std::max(f.max_degree, f.inc_ptr[v + 1]);
         f.inc_ptr[v + 1] += f.inc_ptr[v];
     }
+
+    // Layout of the per-(edge, node) buffer the reduce reads ("slots"):
+    //  * nodes of degree <= kSmallDeg, sorted by decreasing degree (ties by id), form groups
+    //    of 32; group g owns width_g * 32 slots from grp_off[g], and the k-th incidence of the
+    //    group's lane-l node sits at grp_off[g] + 32 k + l (sliced ELL: a warp reads each k
+    //    with one coalesced load; width_g is the group's largest degree, and the slots past
+    //    a lane's own degree are padding that no kernel reads or writes);
+    //  * then every medium node (degree <= kMedDeg) owns a contiguous segment;
+    //  * then every big node, cut into pieces of at most kPiece slots.
+    // Inside a node, incidences are ordered by bucket, then edge, then member.
+    std::vector<int64_t> base(n, 0);
+    std::vector<int32_t> step(n, 1);
     {
-        std::vector<int64_t> fill(f.inc_ptr.begin(), f.inc_ptr.end() - 1);
+        std::vector<int32_t> small;
+        for (int64_t v = 0; v < n; ++v)
+            if (f.inc_ptr[v + 1] - f.inc_ptr[v] <= kSmallDeg) small.push_back((int32_t)v);
+        std::stable_sort(small.begin(), small.end(), [&](int32_t a, int32_t b) {
+            return f.inc_ptr[a + 1] - f.inc_ptr[a] > f.inc_ptr[b + 1] - f.inc_ptr[b];
+        });
+        int64_t off = 0;
+        for (size_t g0 = 0; g0 < small.size(); g0 += 32) {
+            const int32_t w = (int32_t)(f.inc_ptr[small[g0] + 1] - f.inc_ptr[small[g0]]);
+            f.grp_off.push_back(off);
+            for (int l = 0; l < 32; ++l) {
+                size_t i = g0 + l;
+                f.grp_node.push_back(i < small.size() ? small[i] : -1);
+                f.grp_deg.push_back(i < small.size() ? (uint8_t)(f.inc_ptr[small[i] + 1] - f.inc_ptr[small[i]]) : 0);
+                if (i < small.size()) {
+                    base[small[i]] = off + l;
+                    step[small[i]] = 32;
+                }
+            }
+            off += 32 * (int64_t)w;
+        }
+        for (int64_t v = 0; v < n; ++v) {
+            int64_t d = f.inc_ptr[v + 1] - f.inc_ptr[v];
+            if (d > kSmallDeg && d <= kMedDeg) {
+                f.med_node.push_back((int32_t)v);
+                f.med_off.push_back(off);
+                f.med_len.push_back((int32_t)d);
+                base[v] = off;
+                off += d;
+            }
+        }
+        for (int64_t v = 0; v < n; ++v) {
+            int64_t d = f.inc_ptr[v + 1] - f.inc_ptr[v];
+            if (d > kMedDeg) {
+                f.big_node.push_back((int32_t)v);
+                f.big_piece_ptr.push_back((int32_t)f.piece_start.size());
+                base[v] = off;
+                for (int64_t st = 0; st < d; st += kPiece) {
+                    f.piece_start.push_back(off + st);
+                    f.piece_len.push_back((int32_t)std::min<int64_t>(kPiece, d - st));
+                }
+                off += d;
+            }
+        }
+        f.big_piece_ptr.push_back((int32_t)f.piece_start.size());
+        f.buf_len = off;
+    }
+    if (f.buf_len >= (int64_t)INT32_MAX) return fail(S3_EINVAL, "incidence buffer exceeds 2^31 slots");
+    {
+        std::vector<int32_t> kth(n, 0);
         for (const HostBucket &b : f.buckets)
             for (int64_t k = 0; k < b.m; ++k)
                 for (int i = 0; i < b.s; ++i) {
                     int64_t at = b.offset + (int64_t)i * b.ld + k;
-                    f.slot[at] = (int32_t)fill[f.ids[at]]++;
+                    int32_t v = f.ids[at];
+                    f.slot[at] = (int32_t)(base[v] + (int64_t)step[v] * kth[v]++);
                 }
     }
-
-    // deterministic reduce work lists
-    for (int64_t v = 0; v < n; ++v) {
-        int64_t d = f.inc_ptr[v + 1] - f.inc_ptr[v];
-        if (d <= kSmallDeg)
-            f.red_small.push_back((int32_t)v);
-        else if (d <= kMedDeg)
-            f.red_med.push_back((int32_t)v);
-        else {
-            f.big_node.push_back((int32_t)v);
-            f.big_piece_ptr.push_back((int32_t)f.piece_start.size());
-            for (int64_t st = f.inc_ptr[v]; st < f.inc_ptr[v + 1]; st += kPiece) {
-                f.piece_start.push_back(st);
-                f.piece_len.push_back((int32_t)std::min<int64_t>(kPiece, f.inc_ptr[v + 1] - st));
-            }
-        }
-    }
-    f.big_piece_ptr.push_back((int32_t)f.piece_start.size());
 
     // ------------------------------------------------------------- CCSS --
     if (!(opt.build_ccss || opt.layout == S3_LAYOUT_CCSS)) return S3_OK;

@@ -27,13 +27,19 @@ struct s3_graph_s {
     // device format
     int32_t *d_ids = nullptr, *d_slot = nullptr;
     int64_t *d_inc_ptr = nullptr;
-    int32_t *d_small = nullptr, *d_med = nullptr, *d_big_nodes = nullptr, *d_big_piece_ptr = nullptr;
+    int64_t *d_grp_off = nullptr;
+    int32_t *d_grp_node = nullptr;
+    uint8_t *d_grp_deg = nullptr;
+    int32_t *d_med = nullptr, *d_med_len = nullptr;
+    int64_t *d_med_off = nullptr;
+    int32_t *d_big_nodes = nullptr, *d_big_piece_ptr = nullptr;
     int64_t *d_piece_start = nullptr;
     int32_t *d_piece_len = nullptr;
-    int64_t n_small = 0, n_med = 0, n_big = 0, n_pieces = 0;
+    int64_t n_grp = 0, n_med = 0, n_big = 0, n_pieces = 0;
+    int64_t buf_len = 0;            // slots of the per-(edge, node) buffer (nnz plus group padding)
 
     // scratch owned by the handle (reused by every call)
-    void *d_buf = nullptr;          // nnz values (8 bytes each) for the segmented reduce
+    void *d_buf = nullptr;          // buf_len values (8 bytes each) for the segmented reduce
     void *d_partial = nullptr;      // n_pieces partial sums (8 bytes each)
     float *d_comp = nullptr;        // n FP32 compensation terms (atomic mode)
     unsigned long long *d_range = nullptr;
@@ -116,6 +122,28 @@ s3_status run_edges(s3_graph_s *g, s3_dtype dt, const void *x, void *y, int bias
 s3_status run_ccss(s3_graph_s *g, s3_dtype dt, const void *x, void *y, int bias, const int32_t *skip,
                    cudaStream_t st);
 s3_status upload_ccss(s3_graph_s *g, const HostFormat &f);
+
+// Arguments of the segmented reduce over the handle's slot buffer.
+inline ReduceArgs reduce_args(const s3_graph_s *g, const int32_t *skip) {
+    ReduceArgs r{};
+    r.grp_off = g->d_grp_off;
+    r.grp_node = g->d_grp_node;
+    r.grp_deg = g->d_grp_deg;
+    r.n_grp = g->n_grp;
+    r.med_nodes = g->d_med;
+    r.med_off = g->d_med_off;
+    r.med_len = g->d_med_len;
+    r.n_med = g->n_med;
+    r.piece_start = g->d_piece_start;
+    r.piece_len = g->d_piece_len;
+    r.n_pieces = g->n_pieces;
+    r.big_nodes = g->d_big_nodes;
+    r.big_piece_ptr = g->d_big_piece_ptr;
+    r.n_big = g->n_big;
+    r.partial = g->d_partial;
+    r.skip = skip;
+    return r;
+}
 
 }  // namespace s3
 

@@ -58,13 +58,19 @@ struct HostFormat {
     std::vector<HostBucket> buckets;      // non-empty buckets, increasing s
     std::vector<int32_t> ids;             // concatenated SoA member ids
     std::vector<int32_t> slot;            // same layout: position in node-sorted incidence order
-    std::vector<int64_t> inc_ptr;         // n+1: node v owns incidence slots [inc_ptr[v], inc_ptr[v+1])
-    // deterministic reduce work lists
-    std::vector<int32_t> red_small;       // nodes with degree <= kSmallDeg (thread per node)
-    std::vector<int32_t> red_med;         // kSmallDeg < degree <= kMedDeg (warp per node)
+    std::vector<int64_t> inc_ptr;         // n+1: prefix sums of the node degrees
+    // deterministic reduce work lists over the slot buffer
+    // small nodes (degree <= kSmallDeg): groups of 32 in sliced-ELL layout
+    std::vector<int64_t> grp_off;         // first slot of each group
+    std::vector<int32_t> grp_node;        // 32 per group, -1 = padding lane
+    std::vector<uint8_t> grp_deg;         // 32 per group: the lane's degree (0 for padding)
+    // medium nodes (kSmallDeg < degree <= kMedDeg): one warp per node, contiguous segment
+    std::vector<int32_t> med_node, med_len;
+    std::vector<int64_t> med_off;
     std::vector<int32_t> big_node;        // degree > kMedDeg (pieces of at most kPiece slots)
+    int64_t buf_len = 0;                  // slots of the per-(edge, node) buffer (>= nnz)
     std::vector<int32_t> big_piece_ptr;   // pieces of big_node[k]: [big_piece_ptr[k], big_piece_ptr[k+1])
-    std::vector<int64_t> piece_start;     // first incidence slot of each piece
+    std::vector<int64_t> piece_start;     // first slot of each piece
     std::vector<int32_t> piece_len;
     bool has_ccss = false;
     HostCCSS ccss;

@@ -47,10 +47,15 @@ cudaError_t prepare_edge_kernels_f64();
 
 // Deterministic segmented reduce of a node-sorted buffer into y.
 struct ReduceArgs {
-    const int64_t *inc_ptr;        // n+1
-    const int32_t *small_nodes;    // degree <= kSmallDeg
-    int64_t n_small;
-    const int32_t *med_nodes;      // kSmallDeg < degree <= kMedDeg
+    // nodes of degree <= 32: groups of 32 lanes in sliced-ELL layout
+    const int64_t *grp_off;        // n_grp: first slot of the group
+    const int32_t *grp_node;       // 32 n_grp: node of each lane, -1 for padding
+    const uint8_t *grp_deg;        // 32 n_grp: degree of each lane's node
+    int64_t n_grp;
+    // nodes of degree 33..4096: one contiguous segment each
+    const int32_t *med_nodes;
+    const int64_t *med_off;
+    const int32_t *med_len;
     int64_t n_med;
     const int64_t *piece_start;    // pieces of big nodes
     const int32_t *piece_len;

@@ -268,9 +268,6 @@ s3_status s3_hcentrality(s3_graph_t g, const s3_nqz_options *opt_in, const doubl
     if (opt.switch_tol <= 0) opt.switch_tol = 1e-5;
     if (!(opt.tol > 0)) return fail(S3_EINVAL, "tol must be > 0");
     if (g->N < 2) return fail(S3_EINVAL, "NQZ needs rank >= 2");
-    if (g->info.n > 0 && g->n_small > 0) {
-        // isolated nodes have no incidence: the ratio z/x^(N-1) is 0/0 there
-    }
     DeviceGuard guard(g->device);
     cudaStream_t st = (cudaStream_t)stream;
     // graphs cannot be captured on the legacy default stream: use a blocking

@@ -1,9 +1,12 @@
 // Deterministic segmented reduce: y_v = sum of the per-(edge, node) values
-// that the edge kernels wrote into a buffer laid out in node-sorted incidence
-// order (node v owns slots [inc_ptr[v], inc_ptr[v+1])).  The work is split by
-// degree so that hubs do not serialise on one thread:
-//   degree <= 32          one thread per node,
-//   degree <= 4096        one warp per node,
+// that the edge kernels wrote into the slot buffer.  The buffer is laid out
+// by node so that every node's values can be summed without atomics, and the
+// work is split by degree so that hubs do not serialise on one thread:
+//   degree <= 32          groups of 32 nodes of similar degree in sliced-ELL
+//                         layout (the k-th value of lane l at off + 32 k + l):
+//                         one warp per group, lane l sums its own node, and
+//                         every load of the warp is one coalesced 128-byte row;
+//   degree <= 4096        one warp per node over its contiguous segment;
 //   larger                pieces of 4096 slots, one block each, then one
 //                         warp per node adds its pieces in a fixed order.
 // Every thread/warp/block adds in a fixed order, so the result does not
@@ -82,33 +85,35 @@ constexpr int kRedThreads = 256;
 
 template <typename T>
 __global__ void __launch_bounds__(kRedThreads) reduce_kernel(ReduceArgs r, const T *__restrict__ buf, T *__restrict__ y,
-                                                             int64_t nb_small, int64_t nb_med) {
+                                                             int64_t nb_grp, int64_t nb_med) {
     if (r.skip && *r.skip) return;
     using A = typename AccOf<T>::type;
     const int64_t bid = blockIdx.x;
     const int tid = threadIdx.x;
-    if (bid < nb_small) {
-        int64_t i = bid * kRedThreads + tid;
-        if (i >= r.n_small) return;
-        int v = r.small_nodes[i];
-        int64_t b = r.inc_ptr[v], t = r.inc_ptr[v + 1];
+    if (bid < nb_grp) {
+        const int64_t gi = bid * (kRedThreads / 32) + (tid >> 5);
+        if (gi >= r.n_grp) return;
+        const int lane = tid & 31;
+        const int node = r.grp_node[gi * 32 + lane];
+        const int d = r.grp_deg[gi * 32 + lane];
+        const T *p = buf + r.grp_off[gi] + lane;
         A a;
-        int64_t k = b;
-        for (; k + 4 <= t; k += 4) {  // four loads in flight, added in order
-            T v0 = buf[k], v1 = buf[k + 1], v2 = buf[k + 2], v3 = buf[k + 3];
+        int k = 0;
+        for (; k + 4 <= d; k += 4) {  // four coalesced rows in flight, added in order
+            T v0 = p[32 * k], v1 = p[32 * k + 32], v2 = p[32 * k + 64], v3 = p[32 * k + 96];
             a.add(v0);
             a.add(v1);
             a.add(v2);
             a.add(v3);
         }
-        for (; k < t; ++k) a.add(buf[k]);
-        y[v] = (T)a.value();
-    } else if (bid < nb_small + nb_med) {
-        int64_t i = (bid - nb_small) * (kRedThreads / 32) + (tid >> 5);
+        for (; k < d; ++k) a.add(p[32 * k]);
+        if (node >= 0) y[node] = (T)a.value();
+    } else if (bid < nb_grp + nb_med) {
+        int64_t i = (bid - nb_grp) * (kRedThreads / 32) + (tid >> 5);
         if (i >= r.n_med) return;
         const int lane = tid & 31;
-        int v = r.med_nodes[i];
-        int64_t b = r.inc_ptr[v], t = r.inc_ptr[v + 1];
+        const int v = r.med_nodes[i];
+        const int64_t b = r.med_off[i], t = b + r.med_len[i];
         A a;
         int64_t k = b + lane;
         for (; k + 96 < t; k += 128) {  // four loads in flight per lane, added in order
@@ -123,7 +128,7 @@ __global__ void __launch_bounds__(kRedThreads) reduce_kernel(ReduceArgs r, const
         if (lane == 0) y[v] = (T)a.value();
     } else {
         __shared__ A part[kRedThreads / 32];
-        int64_t pc = bid - nb_small - nb_med;
+        int64_t pc = bid - nb_grp - nb_med;
         int64_t b = r.piece_start[pc];
         int len = r.piece_len[pc];
         A a;
@@ -164,11 +169,11 @@ __global__ void finalize_big_kernel(ReduceArgs r, T *__restrict__ y) {
 
 template <typename T>
 cudaError_t launch_reduce_t(const ReduceArgs &r, const T *buf, T *y, cudaStream_t st) {
-    int64_t nb_small = (r.n_small + kRedThreads - 1) / kRedThreads;
+    int64_t nb_grp = (r.n_grp + (kRedThreads / 32) - 1) / (kRedThreads / 32);
     int64_t nb_med = (r.n_med + (kRedThreads / 32) - 1) / (kRedThreads / 32);
-    int64_t grid = nb_small + nb_med + r.n_pieces;
+    int64_t grid = nb_grp + nb_med + r.n_pieces;
     if (grid > 0) {
-        reduce_kernel<T><<<(unsigned)grid, kRedThreads, 0, st>>>(r, buf, y, nb_small, nb_med);
+        reduce_kernel<T><<<(unsigned)grid, kRedThreads, 0, st>>>(r, buf, y, nb_grp, nb_med);
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }
