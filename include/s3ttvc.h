@@ -97,7 +97,10 @@ typedef struct {
                               order of Sec. II-B / Fig. 2), edges in input order */
     int32_t streams;       /* size buckets are spread over this many CUDA streams forked from the
                               caller's stream (1..8); 0 = default (4) */
-    int32_t reserved[7];
+    int32_t small_bucket_edges; /* thread-per-edge buckets of size >= 2 with at most this many edges
+                              share one fused launch (one edge per thread); 0 = default (40000),
+                              negative = every bucket gets its own launch */
+    int32_t reserved[6];
 } s3_options;
 
 typedef enum { S3_ORDER_DEGREE = 0, S3_ORDER_INDEX = 1 } s3_order;

@@ -34,7 +34,7 @@ class s3_options(ctypes.Structure):
     _fields_ = [("rank", ctypes.c_int32), ("reduce", ctypes.c_int32), ("layout", ctypes.c_int32),
                 ("build_ccss", ctypes.c_int32), ("device", ctypes.c_int32), ("thread_max_w", ctypes.c_int32),
                 ("block_threads", ctypes.c_int32), ("order", ctypes.c_int32), ("streams", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 7)]
+                ("small_bucket_edges", ctypes.c_int32), ("reserved", ctypes.c_int32 * 6)]
 
 
 class s3_format_info(ctypes.Structure):

@@ -93,10 +93,34 @@ s3_status run_edges(s3_graph_s *g, s3_dtype dt, const void *x, void *y, int bias
         for (int i = 0; i < ns; ++i) S3_CUDA(cudaStreamWaitEvent(g->aux[i], g->ev_fork, 0));
     }
     double load[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    auto pick = [&](double cost) {
+        if (ns <= 1) return st;
+        int best = 0;
+        for (int i = 1; i < ns; ++i)
+            if (load[i] < load[best]) best = i;
+        load[best] += cost;
+        return g->aux[best];
+    };
+    bool tail_done = g->n_tail == 0;
+    auto launch_tail = [&]() -> s3_status {
+        tail_done = true;
+        cudaStream_t ts = pick(g->tail_cost);
+        cudaError_t e = dt == S3_F32 ? launch_edge_tail_f32(g->d_tail, g->n_tail, g->tail_blocks, g->tail_bs,
+                                                            g->tail_smem[0], (const float *)x, o, ts)
+                                     : launch_edge_tail_f64(g->d_tail, g->n_tail, g->tail_blocks, g->tail_bs,
+                                                            g->tail_smem[1], (const double *)x, o, ts);
+        if (e != cudaSuccess) return cuda_fail(e, "small-bucket launch");
+        ++launches;
+        return S3_OK;
+    };
     for (size_t r = 0; r < g->bucket_order.size(); ++r) {
         const size_t k = g->bucket_order[r];
         const HostBucket &hb = g->buckets[k];
-        if (hb.m <= 0) continue;
+        if (hb.m <= 0 || g->in_tail[k]) continue;
+        if (!tail_done && g->tail_cost >= g->bucket_cost[k]) {
+            s3_status ts = launch_tail();
+            if (ts != S3_OK) return ts;
+        }
         EdgeBucketArgs b{};
         b.ids = g->d_ids + hb.offset;
         b.slot = g->d_slot + hb.offset;
@@ -108,19 +132,16 @@ s3_status run_edges(s3_graph_s *g, s3_dtype dt, const void *x, void *y, int bias
         b.K = g->K[k];
         b.Km = g->Km[k];
         b.Ke = g->Ke[k];
-        cudaStream_t bs = st;
-        if (ns > 1) {
-            int best = 0;
-            for (int i = 1; i < ns; ++i)
-                if (load[i] < load[best]) best = i;
-            load[best] += g->bucket_cost[k];
-            bs = g->aux[best];
-        }
+        cudaStream_t bs = pick(g->bucket_cost[k]);
         cudaError_t e = dt == S3_F32
                             ? launch_edge_bucket_f32(b, (const float *)x, o, g->opt.thread_max_w, g->opt.block_threads, bs)
                             : launch_edge_bucket_f64(b, (const double *)x, o, g->opt.thread_max_w, g->opt.block_threads, bs);
         if (e != cudaSuccess) return cuda_fail(e, "edge kernel launch");
         ++launches;
+    }
+    if (!tail_done) {
+        s3_status ts = launch_tail();
+        if (ts != S3_OK) return ts;
     }
     if (ns > 1) {
         for (int i = 0; i < ns; ++i) {
@@ -134,7 +155,7 @@ s3_status run_edges(s3_graph_s *g, s3_dtype dt, const void *x, void *y, int bias
         cudaError_t e = dt == S3_F32 ? launch_reduce_f32(r, (const float *)g->d_buf, (float *)y, st)
                                      : launch_reduce_f64(r, (const double *)g->d_buf, (double *)y, st);
         if (e != cudaSuccess) return cuda_fail(e, "reduce launch");
-        launches += 1 + (g->n_big > 0 ? 1 : 0);
+        ++launches;
     } else if (dt == S3_F32) {
         cudaError_t e = launch_add_comp((float *)y, g->d_comp, g->n, skip, st);
         if (e != cudaSuccess) return cuda_fail(e, "compensation launch");
@@ -238,14 +259,22 @@ s3_status s3_build_format(int64_t n, int64_t m, const int64_t *edge_ptr, const i
     if ((st = upload(g, &g->d_grp_off, f.grp_off)) != S3_OK) return bail(st);
     if ((st = upload(g, &g->d_grp_node, f.grp_node)) != S3_OK) return bail(st);
     if ((st = upload(g, &g->d_grp_deg, f.grp_deg)) != S3_OK) return bail(st);
+    if ((st = upload(g, &g->d_med8, f.med8_node)) != S3_OK) return bail(st);
+    if ((st = upload(g, &g->d_med8_off, f.med8_off)) != S3_OK) return bail(st);
+    if ((st = upload(g, &g->d_med8_len, f.med8_len)) != S3_OK) return bail(st);
     if ((st = upload(g, &g->d_med, f.med_node)) != S3_OK) return bail(st);
     if ((st = upload(g, &g->d_med_off, f.med_off)) != S3_OK) return bail(st);
     if ((st = upload(g, &g->d_med_len, f.med_len)) != S3_OK) return bail(st);
     if ((st = upload(g, &g->d_big_nodes, f.big_node)) != S3_OK) return bail(st);
     if ((st = upload(g, &g->d_big_piece_ptr, f.big_piece_ptr)) != S3_OK) return bail(st);
+    if ((st = upload(g, &g->d_piece_big, f.piece_big)) != S3_OK) return bail(st);
+    if ((st = dev_alloc(g, &g->d_big_count, f.big_node.size())) != S3_OK) return bail(st);
+    if (!f.big_node.empty() && cudaMemset(g->d_big_count, 0, sizeof(int32_t) * f.big_node.size()) != cudaSuccess)
+        return bail(cuda_fail(cudaGetLastError(), "memset"));
     if ((st = upload(g, &g->d_piece_start, f.piece_start)) != S3_OK) return bail(st);
     if ((st = upload(g, &g->d_piece_len, f.piece_len)) != S3_OK) return bail(st);
     g->n_grp = (int64_t)f.grp_off.size();
+    g->n_med8 = (int64_t)f.med8_node.size();
     g->n_med = (int64_t)f.med_node.size();
     g->n_big = (int64_t)f.big_node.size();
     g->n_pieces = (int64_t)f.piece_start.size();
@@ -285,6 +314,50 @@ s3_status s3_build_format(int64_t n, int64_t m, const int64_t *edge_ptr, const i
     }
     std::stable_sort(g->bucket_order.begin(), g->bucket_order.end(),
                      [&](size_t a, size_t b) { return g->bucket_cost[a] > g->bucket_cost[b]; });
+    // small thread-per-edge buckets: one fused launch.  A bucket of a few thousand
+    // edges costs about as much as one edge's latency chain; fused, that latency is
+    // paid once per call instead of once per bucket.
+    {
+        const int64_t lim = o.small_bucket_edges == 0 ? 40000 : o.small_bucket_edges;
+        const int wmax = (o.thread_max_w <= 0 || o.thread_max_w > 32) ? 32 : o.thread_max_w;
+        g->in_tail.assign(g->buckets.size(), 0);
+        std::vector<TailEntry> tab;
+        for (size_t k = 0; k < g->buckets.size(); ++k) {
+            const HostBucket &hb = g->buckets[k];
+            const int W = g->N - hb.s + 1;
+            if (hb.s < 2 || hb.m <= 0 || hb.m > lim || W > wmax) continue;
+            if (edge_tail_smem_words(hb.s, W, 8) * 4 * (size_t)g->tail_bs > kEdgeSmemCap) continue;
+            TailEntry t{};
+            t.b.ids = g->d_ids + hb.offset;
+            t.b.slot = g->d_slot + hb.offset;
+            t.b.m = hb.m;
+            t.b.ld = hb.ld;
+            t.b.s = hb.s;
+            t.b.N = g->N;
+            t.b.target = g->target[k];
+            t.b.K = g->K[k];
+            t.b.Km = g->Km[k];
+            t.b.Ke = g->Ke[k];
+            t.W = W;
+            t.block0 = g->tail_blocks;
+            g->tail_blocks += (hb.m + g->tail_bs - 1) / g->tail_bs;
+            for (int d = 0; d < 2; ++d)
+                g->tail_smem[d] = std::max(g->tail_smem[d], edge_tail_smem_words(hb.s, W, d ? 8 : 4) * 4 * (size_t)g->tail_bs);
+            g->tail_cost += g->bucket_cost[k];
+            g->in_tail[k] = 1;
+            tab.push_back(t);
+        }
+        if (tab.size() == 1) {  // a lone small bucket keeps its own kernel
+            g->in_tail.assign(g->buckets.size(), 0);
+            tab.clear();
+            g->tail_blocks = 0;
+            g->tail_cost = 0.0;
+        }
+        if (!tab.empty()) {
+            if ((st = upload(g, &g->d_tail, tab)) != S3_OK) return bail(st);
+            g->n_tail = (int32_t)tab.size();
+        }
+    }
     g->info.device_bytes = g->device_bytes;
     *out = g;
     return S3_OK;

@@ -44,7 +44,8 @@ using ReduceGraph = ReduceArgs;
 
 struct ReduceTile {
     int32_t graph;
-    int32_t kind;   // 0: 8 groups of 32 small nodes, 1: 8 medium nodes, 2: one hub piece
+    int32_t kind;   // 0: 8 groups of 32 small nodes, 1: 8 medium nodes, 2: one hub piece,
+                    // 3: 32 medium nodes of degree <= 128
     int64_t first;
 };
 

@@ -340,6 +340,7 @@ s3_status s3_batch_create(int32_t count, const s3_graph_t *graphs, int32_t nvec,
         rg[gi] = reduce_args(g, nullptr);
         for (int64_t f = 0; f < g->n_pieces; ++f) rtiles.push_back({gi, 2, f});
         for (int64_t f = 0; f < g->n_med; f += 8) rtiles.push_back({gi, 1, f});
+        for (int64_t f = 0; f < g->n_med8; f += 32) rtiles.push_back({gi, 3, f});
         for (int64_t f = 0; f < g->n_grp; f += 8) rtiles.push_back({gi, 0, f});
         for (int64_t k = 0; k < g->n_big; ++k) finals.push_back({gi, (int32_t)k});
     }

@@ -18,16 +18,18 @@ __device__ __forceinline__ void batch_thread_tile(const BatchEdgeArgs &a, const 
                                                   unsigned char *smem_raw) {
     const EdgeBucketArgs &b = bb.b;
     const int BS = blockDim.x;
-    const int tid = threadIdx.x;
+    const int tid = threadIdx.x, lane = tid & 31;
     const int s = b.s;
     const int nv = a.nvec;
-    T *tb = reinterpret_cast<T *>(smem_raw);
-    T *Xb0 = tb + tid;
-    T *Xb1 = tb + (size_t)s * BS + tid;
-    T *Pre = tb + (size_t)2 * s * BS + tid;
-    int32_t *ibase = reinterpret_cast<int32_t *>(tb + (size_t)(2 * s + (s > 2 ? (s - 2) * W : 0)) * BS) + tid;
-    auto ids_of = [&](int r) { return ibase + (size_t)r * s * BS; };
-    auto slots_of = [&](int r) { return ibase + (size_t)(3 + r) * s * BS; };
+    // per-warp regions, as in edge_thread_kernel
+    const size_t words = thread_smem_words<T>(s, W);
+    T *wb = reinterpret_cast<T *>(smem_raw + (size_t)(tid >> 5) * words * 4 * kLS);
+    T *Xb0 = wb + lane;
+    T *Xb1 = Xb0 + s * kLS;
+    T *Pre = Xb0 + 2 * s * kLS;
+    int32_t *ibase = reinterpret_cast<int32_t *>(wb + (2 * s + (s > 2 ? (s - 2) * W : 0)) * kLS) + lane;
+    auto ids_of = [&](int r) { return ibase + r * s * kLS; };
+    auto slots_of = [&](int r) { return ibase + (3 + r) * s * kLS; };
     const int64_t end = tl.e0 + tl.count;
     int64_t e = tl.e0 + tid;
     if (e >= end) return;
@@ -39,8 +41,8 @@ __device__ __forceinline__ void batch_thread_tile(const BatchEdgeArgs &a, const 
         const int64_t ee = edge_at(k);
         int32_t *ib = ids_of(r), *sb = slots_of(r);
         for (int i = 0; i < s; ++i) {
-            cp_async<4>(ib + (size_t)i * BS, b.ids + (int64_t)i * b.ld + ee);
-            cp_async<4>(sb + (size_t)i * BS, b.slot + (int64_t)i * b.ld + ee);
+            cp_async<4>(ib + i * kLS, b.ids + (int64_t)i * b.ld + ee);
+            cp_async<4>(sb + i * kLS, b.slot + (int64_t)i * b.ld + ee);
         }
     };
     auto issue_x = [&](int64_t item, T *xb) {
@@ -48,7 +50,7 @@ __device__ __forceinline__ void batch_thread_tile(const BatchEdgeArgs &a, const 
         const int v = (int)(item - k * nv);
         const T *x = reinterpret_cast<const T *>(a.xs[(size_t)bb.graph * nv + v]);
         const int32_t *ib = ids_of((int)(k % 3));
-        for (int i = 0; i < s; ++i) cp_async<(int)sizeof(T)>(xb + (size_t)i * BS, x + ib[(size_t)i * BS]);
+        for (int i = 0; i < s; ++i) cp_async<(int)sizeof(T)>(xb + i * kLS, x + ib[i * kLS]);
     };
     issue_ids(0, 0);
     cp_async_commit();
@@ -69,7 +71,7 @@ __device__ __forceinline__ void batch_thread_tile(const BatchEdgeArgs &a, const 
         if (v == 0 && k + 2 < nedges) issue_ids(k + 2, (int)((k + 2) % 3));
         cp_async_commit();
         o.out = a.bufs[(size_t)bb.graph * nv + v];
-        edge_compute<T, W, true>(b, o, xc, Pre, ids_of((int)(k % 3)), slots_of((int)(k % 3)), BS, s);
+        edge_compute<T, W, true>(b, o, xc, Pre, ids_of((int)(k % 3)), slots_of((int)(k % 3)), s);
     }
     cp_async_wait_all();
 }
@@ -246,6 +248,18 @@ __global__ void __launch_bounds__(256) batch_reduce_kernel(BatchReduceArgs a) {
                     for (int d = 16; d > 0; d >>= 1) acc.merge(acc.down(d));
                     if (lane == 0) y[node] = (T)acc.value();
                 }
+            } else if (rt.kind == 3) {
+                // eight lanes per node; lanes of a missing node join the shuffles only
+                const int64_t i = rt.first + (tid >> 3);
+                const bool has = i < g.n_med8;
+                const int sl = tid & 7;
+                const int64_t b = has ? g.med8_off[i] : 0;
+                const int len = has ? g.med8_len[i] : 0;
+                A acc;
+                for (int k = sl; k < len; k += 8) acc.add(buf[b + k]);
+#pragma unroll
+                for (int d = 4; d > 0; d >>= 1) acc.merge(acc.down(d));
+                if (has && sl == 0) y[g.med8_nodes[i]] = (T)acc.value();
             } else {
                 const int64_t pc = rt.first;
                 int64_t b = g.piece_start[pc];

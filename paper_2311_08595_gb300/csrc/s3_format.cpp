@@ -177,7 +177,8 @@ s3_status build_host_format(int64_t n, int64_t m, const int64_t *edge_ptr, const
     //    group's lane-l node sits at grp_off[g] + 32 k + l (sliced ELL: a warp reads each k
     //    with one coalesced load; width_g is the group's largest degree, and the slots past
     //    a lane's own degree are padding that no kernel reads or writes);
-    //  * then every medium node (degree <= kMedDeg) owns a contiguous segment;
+    //  * then every medium node (degree <= kMedDeg) owns a contiguous segment
+    //    (read by eight lanes up to kMed8Deg, by a warp above);
     //  * then every big node, cut into pieces of at most kPiece slots.
     // Inside a node, incidences are ordered by bucket, then edge, then member.
     std::vector<int64_t> base(n, 0);
@@ -207,9 +208,9 @@ s3_status build_host_format(int64_t n, int64_t m, const int64_t *edge_ptr, const
         for (int64_t v = 0; v < n; ++v) {
             int64_t d = f.inc_ptr[v + 1] - f.inc_ptr[v];
             if (d > kSmallDeg && d <= kMedDeg) {
-                f.med_node.push_back((int32_t)v);
-                f.med_off.push_back(off);
-                f.med_len.push_back((int32_t)d);
+                (d <= kMed8Deg ? f.med8_node : f.med_node).push_back((int32_t)v);
+                (d <= kMed8Deg ? f.med8_off : f.med_off).push_back(off);
+                (d <= kMed8Deg ? f.med8_len : f.med_len).push_back((int32_t)d);
                 base[v] = off;
                 off += d;
             }
@@ -222,6 +223,7 @@ s3_status build_host_format(int64_t n, int64_t m, const int64_t *edge_ptr, const
                 base[v] = off;
                 for (int64_t st = 0; st < d; st += kPiece) {
                     f.piece_start.push_back(off + st);
+                    f.piece_big.push_back((int32_t)(f.big_node.size() - 1));
                     f.piece_len.push_back((int32_t)std::min<int64_t>(kPiece, d - st));
                 }
                 off += d;

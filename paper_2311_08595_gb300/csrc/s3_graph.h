@@ -30,12 +30,15 @@ struct s3_graph_s {
     int64_t *d_grp_off = nullptr;
     int32_t *d_grp_node = nullptr;
     uint8_t *d_grp_deg = nullptr;
+    int32_t *d_med8 = nullptr, *d_med8_len = nullptr;
+    int64_t *d_med8_off = nullptr;
     int32_t *d_med = nullptr, *d_med_len = nullptr;
     int64_t *d_med_off = nullptr;
-    int32_t *d_big_nodes = nullptr, *d_big_piece_ptr = nullptr;
+    int32_t *d_big_nodes = nullptr, *d_big_piece_ptr = nullptr, *d_piece_big = nullptr;
+    int32_t *d_big_count = nullptr;  // n_big, zero between calls
     int64_t *d_piece_start = nullptr;
     int32_t *d_piece_len = nullptr;
-    int64_t n_grp = 0, n_med = 0, n_big = 0, n_pieces = 0;
+    int64_t n_grp = 0, n_med8 = 0, n_med = 0, n_big = 0, n_pieces = 0;
     int64_t buf_len = 0;            // slots of the per-(edge, node) buffer (nnz plus group padding)
 
     // scratch owned by the handle (reused by every call)
@@ -77,6 +80,14 @@ struct s3_graph_s {
     cudaEvent_t ev_join[8] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
     std::vector<size_t> bucket_order;
     std::vector<double> bucket_cost;
+    // small buckets fused into one launch (one edge per thread)
+    std::vector<char> in_tail;          // per bucket
+    s3::TailEntry *d_tail = nullptr;    // device table, ascending block0
+    int32_t n_tail = 0;
+    int32_t tail_bs = 64;
+    int64_t tail_blocks = 0;
+    size_t tail_smem[2] = {0, 0};       // dynamic shared memory of the launch (FP32, FP64)
+    double tail_cost = 0.0;
     std::vector<void *> allocations;
     int64_t device_bytes = 0;
 };
@@ -130,6 +141,10 @@ inline ReduceArgs reduce_args(const s3_graph_s *g, const int32_t *skip) {
     r.grp_node = g->d_grp_node;
     r.grp_deg = g->d_grp_deg;
     r.n_grp = g->n_grp;
+    r.med8_nodes = g->d_med8;
+    r.med8_off = g->d_med8_off;
+    r.med8_len = g->d_med8_len;
+    r.n_med8 = g->n_med8;
     r.med_nodes = g->d_med;
     r.med_off = g->d_med_off;
     r.med_len = g->d_med_len;
@@ -139,6 +154,8 @@ inline ReduceArgs reduce_args(const s3_graph_s *g, const int32_t *skip) {
     r.n_pieces = g->n_pieces;
     r.big_nodes = g->d_big_nodes;
     r.big_piece_ptr = g->d_big_piece_ptr;
+    r.piece_big = g->d_piece_big;
+    r.big_count = g->d_big_count;
     r.n_big = g->n_big;
     r.partial = g->d_partial;
     r.skip = skip;

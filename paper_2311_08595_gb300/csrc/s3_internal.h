@@ -64,21 +64,26 @@ struct HostFormat {
     std::vector<int64_t> grp_off;         // first slot of each group
     std::vector<int32_t> grp_node;        // 32 per group, -1 = padding lane
     std::vector<uint8_t> grp_deg;         // 32 per group: the lane's degree (0 for padding)
-    // medium nodes (kSmallDeg < degree <= kMedDeg): one warp per node, contiguous segment
+    // medium nodes (kSmallDeg < degree <= kMedDeg), each a contiguous segment:
+    // up to kMed8Deg eight lanes per node (med8_*), above one warp per node (med_*)
+    std::vector<int32_t> med8_node, med8_len;
+    std::vector<int64_t> med8_off;
     std::vector<int32_t> med_node, med_len;
     std::vector<int64_t> med_off;
     std::vector<int32_t> big_node;        // degree > kMedDeg (pieces of at most kPiece slots)
     int64_t buf_len = 0;                  // slots of the per-(edge, node) buffer (>= nnz)
     std::vector<int32_t> big_piece_ptr;   // pieces of big_node[k]: [big_piece_ptr[k], big_piece_ptr[k+1])
     std::vector<int64_t> piece_start;     // first slot of each piece
+    std::vector<int32_t> piece_big;       // index into big_node of each piece's node
     std::vector<int32_t> piece_len;
     bool has_ccss = false;
     HostCCSS ccss;
 };
 
 constexpr int kSmallDeg = 32;
-constexpr int kMedDeg = 4096;
-constexpr int kPiece = 4096;
+constexpr int kMed8Deg = 128;
+constexpr int kMedDeg = 1024;
+constexpr int kPiece = 2048;
 
 s3_status build_host_format(int64_t n, int64_t m, const int64_t *edge_ptr, const int32_t *members,
                             const s3_options &opt, HostFormat &out);

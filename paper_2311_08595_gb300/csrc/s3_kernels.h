@@ -20,6 +20,15 @@ struct EdgeBucketArgs {
     int32_t Ke;
 };
 
+// One small bucket of the fused small-bucket launch (device table, built once
+// per handle): its edges occupy blocks [block0, block0 + ceil(m / threads)).
+struct TailEntry {
+    EdgeBucketArgs b;
+    int32_t W;            // N - s + 1
+    int32_t pad;
+    int64_t block0;
+};
+
 enum OutMode : int32_t {
     kOutBuffer = 0,       // out[slot] = c
     kOutAtomic = 1,       // out[v] += c (atomics)
@@ -41,6 +50,19 @@ cudaError_t launch_edge_bucket_f32(const EdgeBucketArgs &b, const float *x, cons
                                    int thread_max_w, int block_threads, cudaStream_t st);
 cudaError_t launch_edge_bucket_f64(const EdgeBucketArgs &b, const double *x, const EdgeOutArgs &o,
                                    int thread_max_w, int block_threads, cudaStream_t st);
+// Fused launch of small buckets: tab (device) lists ntab buckets by ascending
+// block0; nblocks blocks of bs threads; smem bytes of dynamic shared memory,
+// bs * the largest edge_tail_smem_words of the entries * 4.
+cudaError_t launch_edge_tail_f32(const TailEntry *tab, int ntab, int64_t nblocks, int bs, size_t smem,
+                                 const float *x, const EdgeOutArgs &o, cudaStream_t st);
+cudaError_t launch_edge_tail_f64(const TailEntry *tab, int ntab, int64_t nblocks, int bs, size_t smem,
+                                 const double *x, const EdgeOutArgs &o, cudaStream_t st);
+// 4-byte words of shared memory per thread of the fused launch for an edge of size s
+// and window W, values of value_bytes bytes.
+inline size_t edge_tail_smem_words(int s, int W, int value_bytes) {
+    return (size_t)(s + (s > 2 ? (s - 2) * W : 0)) * (size_t)value_bytes / 4 + (size_t)2 * s;
+}
+constexpr size_t kEdgeSmemCap = 96 * 1024;   // dynamic shared memory per block of the thread kernels
 // One-time per-device set-up (shared-memory limits of the kernels).
 cudaError_t prepare_edge_kernels_f32();
 cudaError_t prepare_edge_kernels_f64();
@@ -52,7 +74,12 @@ struct ReduceArgs {
     const int32_t *grp_node;       // 32 n_grp: node of each lane, -1 for padding
     const uint8_t *grp_deg;        // 32 n_grp: degree of each lane's node
     int64_t n_grp;
-    // nodes of degree 33..4096: one contiguous segment each
+    // nodes of degree 33..128: one contiguous segment each, eight lanes per node
+    const int32_t *med8_nodes;
+    const int64_t *med8_off;
+    const int32_t *med8_len;
+    int64_t n_med8;
+    // nodes of degree 129..1024: one contiguous segment each, a warp per node
     const int32_t *med_nodes;
     const int64_t *med_off;
     const int32_t *med_len;
@@ -62,6 +89,8 @@ struct ReduceArgs {
     int64_t n_pieces;
     const int32_t *big_nodes;
     const int32_t *big_piece_ptr;  // n_big + 1
+    const int32_t *piece_big;      // n_pieces: the big node (index into big_nodes) of each piece
+    int32_t *big_count;            // n_big counters, zero between calls: pieces done this call
     int64_t n_big;
     void *partial;                 // n_pieces partial sums (float2 for FP32, double for FP64)
     const int32_t *skip;

@@ -6,9 +6,11 @@
 //                         layout (the k-th value of lane l at off + 32 k + l):
 //                         one warp per group, lane l sums its own node, and
 //                         every load of the warp is one coalesced 128-byte row;
-//   degree <= 4096        one warp per node over its contiguous segment;
-//   larger                pieces of 4096 slots, one block each, then one
-//                         warp per node adds its pieces in a fixed order.
+//   degree <= 128         eight lanes per node over its contiguous segment;
+//   degree <= 1024        one warp per node over its contiguous segment;
+//   larger                pieces of 2048 slots, one block each; the block that
+//                         finishes a node's last piece (a per-node counter)
+//                         adds the node's piece sums in a fixed order.
 // Every thread/warp/block adds in a fixed order, so the result does not
 // depend on scheduling.  FP32 sums carry a two-sum compensation term.
 #include <cuda_runtime.h>
@@ -64,6 +66,15 @@ __device__ __forceinline__ A warp_reduce(A a) {
     return a;  // lane 0 holds the total
 }
 
+// Sum over each aligned group of 8 lanes (all 32 lanes take part); the group's
+// first lane holds its total.
+template <typename A>
+__device__ __forceinline__ A group8_reduce(A a) {
+#pragma unroll
+    for (int d = 4; d > 0; d >>= 1) a.merge(shfl_down_acc(a, d));
+    return a;
+}
+
 __device__ __forceinline__ void store_partial(void *p, int64_t i, const AccF &a) {
     reinterpret_cast<float2 *>(p)[i] = make_float2(a.s, a.c);
 }
@@ -71,114 +82,139 @@ __device__ __forceinline__ void store_partial(void *p, int64_t i, const AccD &a)
     reinterpret_cast<double *>(p)[i] = a.s;
 }
 __device__ __forceinline__ void load_partial(const void *p, int64_t i, AccF &a) {
-    float2 v = reinterpret_cast<const float2 *>(p)[i];
+    float2 v = __ldcg(reinterpret_cast<const float2 *>(p) + i);
     AccF t;
     t.s = v.x;
     t.c = v.y;
     a.merge(t);
 }
 __device__ __forceinline__ void load_partial(const void *p, int64_t i, AccD &a) {
-    a.s += reinterpret_cast<const double *>(p)[i];
+    a.s += __ldcg(reinterpret_cast<const double *>(p) + i);
 }
 
 constexpr int kRedThreads = 256;
 
+// Eight loads in flight per thread (then added in order): the kernel is bound
+// by memory latency, not by its few flops.
+constexpr int kRedUnroll = 8;
+
+// Blocks [0, n_pieces): one hub piece each (the longest-running blocks start
+// first); then one warp per medium node of degree > 128; then eight lanes per
+// medium node of degree <= 128; then one warp per group of 32 small nodes.
 template <typename T>
 __global__ void __launch_bounds__(kRedThreads) reduce_kernel(ReduceArgs r, const T *__restrict__ buf, T *__restrict__ y,
-                                                             int64_t nb_grp, int64_t nb_med) {
+                                                             int64_t nb_med, int64_t nb_med8, int64_t nb_grp) {
     if (r.skip && *r.skip) return;
     using A = typename AccOf<T>::type;
+    constexpr int U = kRedUnroll;
     const int64_t bid = blockIdx.x;
     const int tid = threadIdx.x;
-    if (bid < nb_grp) {
-        const int64_t gi = bid * (kRedThreads / 32) + (tid >> 5);
+    const int lane = tid & 31;
+    if (bid < r.n_pieces) {
+        __shared__ A part[kRedThreads / 32];
+        const int64_t pc = bid;
+        const T *p = buf + r.piece_start[pc];
+        const int len = r.piece_len[pc];
+        A a;
+        int k = tid;
+        for (; k + (U - 1) * kRedThreads < len; k += U * kRedThreads) {
+            T v[U];
+#pragma unroll
+            for (int u = 0; u < U; ++u) v[u] = p[k + u * kRedThreads];
+#pragma unroll
+            for (int u = 0; u < U; ++u) a.add(v[u]);
+        }
+        for (; k < len; k += kRedThreads) a.add(p[k]);
+        a = warp_reduce(a);
+        if (lane == 0) part[tid >> 5] = a;
+        __syncthreads();
+        __shared__ int last;
+        const int hb = r.piece_big[pc];
+        if (tid == 0) {
+            A tot = part[0];
+            for (int w = 1; w < kRedThreads / 32; ++w) tot.merge(part[w]);
+            store_partial(r.partial, pc, tot);
+            __threadfence();
+            const int npc = r.big_piece_ptr[hb + 1] - r.big_piece_ptr[hb];
+            last = atomicAdd(r.big_count + hb, 1) == npc - 1;
+        }
+        __syncthreads();
+        // the block that completes a node's last piece adds the node's partials, lane l
+        // taking pieces l, l+32, ... in order and a fixed shuffle tree after: the same
+        // sum whichever block gets there last
+        if (last && tid < 32) {
+            __threadfence();
+            if (lane == 0) r.big_count[hb] = 0;  // ready for the next call
+            A t;
+            for (int q = r.big_piece_ptr[hb] + lane; q < r.big_piece_ptr[hb + 1]; q += 32) load_partial(r.partial, q, t);
+            t = warp_reduce(t);
+            if (lane == 0) y[r.big_nodes[hb]] = (T)t.value();
+        }
+    } else if (bid < r.n_pieces + nb_med) {
+        const int64_t i = (bid - r.n_pieces) * (kRedThreads / 32) + (tid >> 5);
+        if (i >= r.n_med) return;
+        const int v = r.med_nodes[i];
+        const T *p = buf + r.med_off[i];
+        const int len = r.med_len[i];
+        A a;
+        int k = lane;
+        for (; k + (U - 1) * 32 < len; k += U * 32) {
+            T w[U];
+#pragma unroll
+            for (int u = 0; u < U; ++u) w[u] = p[k + u * 32];
+#pragma unroll
+            for (int u = 0; u < U; ++u) a.add(w[u]);
+        }
+        for (; k < len; k += 32) a.add(p[k]);
+        a = warp_reduce(a);
+        if (lane == 0) y[v] = (T)a.value();
+    } else if (bid < r.n_pieces + nb_med + nb_med8) {
+        // eight lanes per node; lanes of a missing node read nothing but join the shuffles
+        const int64_t i = (bid - r.n_pieces - nb_med) * (kRedThreads / 8) + (tid >> 3);
+        const bool has = i < r.n_med8;
+        const int sl = tid & 7;
+        const T *p = has ? buf + r.med8_off[i] : buf;
+        const int len = has ? r.med8_len[i] : 0;
+        A a;
+        int k = sl;
+        for (; k + (U - 1) * 8 < len; k += U * 8) {
+            T w[U];
+#pragma unroll
+            for (int u = 0; u < U; ++u) w[u] = p[k + u * 8];
+#pragma unroll
+            for (int u = 0; u < U; ++u) a.add(w[u]);
+        }
+        for (; k < len; k += 8) a.add(p[k]);
+        a = group8_reduce(a);
+        if (has && sl == 0) y[r.med8_nodes[i]] = (T)a.value();
+    } else {
+        const int64_t gi = (bid - r.n_pieces - nb_med - nb_med8) * (kRedThreads / 32) + (tid >> 5);
         if (gi >= r.n_grp) return;
-        const int lane = tid & 31;
         const int node = r.grp_node[gi * 32 + lane];
         const int d = r.grp_deg[gi * 32 + lane];
         const T *p = buf + r.grp_off[gi] + lane;
         A a;
         int k = 0;
-        for (; k + 4 <= d; k += 4) {  // four coalesced rows in flight, added in order
-            T v0 = p[32 * k], v1 = p[32 * k + 32], v2 = p[32 * k + 64], v3 = p[32 * k + 96];
-            a.add(v0);
-            a.add(v1);
-            a.add(v2);
-            a.add(v3);
+        for (; k + U <= d; k += U) {  // U coalesced rows in flight, added in order
+            T w[U];
+#pragma unroll
+            for (int u = 0; u < U; ++u) w[u] = p[32 * (k + u)];
+#pragma unroll
+            for (int u = 0; u < U; ++u) a.add(w[u]);
         }
         for (; k < d; ++k) a.add(p[32 * k]);
         if (node >= 0) y[node] = (T)a.value();
-    } else if (bid < nb_grp + nb_med) {
-        int64_t i = (bid - nb_grp) * (kRedThreads / 32) + (tid >> 5);
-        if (i >= r.n_med) return;
-        const int lane = tid & 31;
-        const int v = r.med_nodes[i];
-        const int64_t b = r.med_off[i], t = b + r.med_len[i];
-        A a;
-        int64_t k = b + lane;
-        for (; k + 96 < t; k += 128) {  // four loads in flight per lane, added in order
-            T v0 = buf[k], v1 = buf[k + 32], v2 = buf[k + 64], v3 = buf[k + 96];
-            a.add(v0);
-            a.add(v1);
-            a.add(v2);
-            a.add(v3);
-        }
-        for (; k < t; k += 32) a.add(buf[k]);
-        a = warp_reduce(a);
-        if (lane == 0) y[v] = (T)a.value();
-    } else {
-        __shared__ A part[kRedThreads / 32];
-        int64_t pc = bid - nb_grp - nb_med;
-        int64_t b = r.piece_start[pc];
-        int len = r.piece_len[pc];
-        A a;
-        int k = tid;
-        for (; k + 3 * kRedThreads < len; k += 4 * kRedThreads) {
-            T v0 = buf[b + k], v1 = buf[b + k + kRedThreads], v2 = buf[b + k + 2 * kRedThreads],
-              v3 = buf[b + k + 3 * kRedThreads];
-            a.add(v0);
-            a.add(v1);
-            a.add(v2);
-            a.add(v3);
-        }
-        for (; k < len; k += kRedThreads) a.add(buf[b + k]);
-        a = warp_reduce(a);
-        if ((tid & 31) == 0) part[tid >> 5] = a;
-        __syncthreads();
-        if (tid == 0) {
-            A tot = part[0];
-            for (int w = 1; w < kRedThreads / 32; ++w) tot.merge(part[w]);
-            store_partial(r.partial, pc, tot);
-        }
     }
-}
-
-// one warp per big node: lane l adds pieces l, l+32, ... in order, then a fixed shuffle tree
-template <typename T>
-__global__ void finalize_big_kernel(ReduceArgs r, T *__restrict__ y) {
-    if (r.skip && *r.skip) return;
-    using A = typename AccOf<T>::type;
-    int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int lane = threadIdx.x & 31;
-    if (i >= r.n_big) return;
-    A a;
-    for (int p = r.big_piece_ptr[i] + lane; p < r.big_piece_ptr[i + 1]; p += 32) load_partial(r.partial, p, a);
-    a = warp_reduce(a);
-    if (lane == 0) y[r.big_nodes[i]] = (T)a.value();
 }
 
 template <typename T>
 cudaError_t launch_reduce_t(const ReduceArgs &r, const T *buf, T *y, cudaStream_t st) {
     int64_t nb_grp = (r.n_grp + (kRedThreads / 32) - 1) / (kRedThreads / 32);
     int64_t nb_med = (r.n_med + (kRedThreads / 32) - 1) / (kRedThreads / 32);
-    int64_t grid = nb_grp + nb_med + r.n_pieces;
+    int64_t nb_med8 = (r.n_med8 + (kRedThreads / 8) - 1) / (kRedThreads / 8);
+    int64_t grid = nb_grp + nb_med + nb_med8 + r.n_pieces;
     if (grid > 0) {
-        reduce_kernel<T><<<(unsigned)grid, kRedThreads, 0, st>>>(r, buf, y, nb_grp, nb_med);
-        cudaError_t e = cudaGetLastError();
-        if (e != cudaSuccess) return e;
-    }
-    if (r.n_big > 0) {
-        finalize_big_kernel<T><<<(unsigned)((r.n_big * 32 + 127) / 128), 128, 0, st>>>(r, y);
+        reduce_kernel<T><<<(unsigned)grid, kRedThreads, 0, st>>>(r, buf, y, nb_med, nb_med8, nb_grp);
         return cudaGetLastError();
     }
     return cudaSuccess;

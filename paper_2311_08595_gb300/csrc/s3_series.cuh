@@ -22,12 +22,18 @@
 
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cfloat>
 #include <cstdint>
 
 #include "s3_kernels.h"
 
 namespace s3 {
+
+// Window widths with a compile-time kernel instance (one thread per edge).
+#define S3_W_CASES(M) \
+    M(1) M(2) M(3) M(4) M(5) M(6) M(7) M(8) M(9) M(10) M(11) M(12) M(13) M(14) M(15) M(16) \
+    M(17) M(18) M(19) M(20) M(21) M(22) M(23) M(24) M(25) M(26) M(27) M(28) M(29) M(30) M(31) M(32)
 
 // ------------------------------------------------------------ arithmetic --
 
@@ -257,61 +263,117 @@ __device__ __forceinline__ void emit_value(const EdgeBucketArgs &b, const EdgeOu
     }
 }
 
-// All contributions of one edge.  Xs[i*BS]: the member values; Pre: this
-// thread's column for Pre_2..Pre_{s-1}; ib/sb: this thread's member ids /
-// incidence slots (stride BS).
+// Output scaling of one edge.  Without the per-node bias every result of the
+// edge is multiplied by the same K 2^(-p(N-1)); when that factor is a normal
+// number it is formed once (exactly: a power-of-two scaling) and each result
+// costs one multiply, the same rounding as scale_result.  Otherwise (and in
+// biased mode) each result goes through scale_result.
+template <typename T> struct EdgeScale {
+    T mult;
+    bool fast;
+};
+
+__device__ __forceinline__ EdgeScale<float> edge_scale(const EdgeBucketArgs &b, const EdgeOutArgs &o, int p, float) {
+    EdgeScale<float> r;
+    const int ex = b.Ke - p * (b.N - 1);
+    r.fast = !o.bias && ex >= -125 && ex <= 127;  // Km 2^ex normal (Km in [0.5, 1))
+    r.mult = b.Km * Arith<float>::pow2(ex);
+    return r;
+}
+__device__ __forceinline__ EdgeScale<double> edge_scale(const EdgeBucketArgs &b, const EdgeOutArgs &o, int p,
+                                                        double) {
+    EdgeScale<double> r;
+    const int ex = -p * (b.N - 1);
+    r.mult = (ex >= -1022 && ex <= 1023) ? b.K * Arith<double>::pow2(ex) : 0.0;
+    r.fast = !o.bias && r.mult >= DBL_MIN && r.mult <= DBL_MAX;
+    return r;
+}
+
+// 1 if c is not a positive normal number (zero, subnormal, infinite or NaN).
+__device__ __forceinline__ int not_normal_pos(float c) {
+    return (__float_as_uint(c) - 0x00800000u) >= 0x7f000000u;
+}
+__device__ __forceinline__ int not_normal_pos(double c) {
+    return ((unsigned long long)__double_as_longlong(c) - 0x0010000000000000ull) >= 0x7fe0000000000000ull;
+}
+
+// Store (or add) one result on the fast path; nbad counts results of positive
+// values that left the normal range (reported once per edge).
+template <typename T, bool BUF>
+__device__ __forceinline__ void emit_fast(const EdgeOutArgs &o, int t, T val, T mult, int &nbad) {
+    const T c = val * mult;
+    nbad += (val > T(0)) & not_normal_pos(c);
+    if constexpr (BUF) {
+        reinterpret_cast<T *>(o.out)[t] = c;
+    } else {
+        scatter_atomic<T>(o, t, c);
+    }
+}
+
+// Shared-memory layout of the thread-per-edge kernels: every warp owns a
+// region in which element k of lane l sits at k * kLS + l, so that a lane's
+// elements are a compile-time stride apart (immediate offsets) and a warp's
+// accesses to one k hit 32 consecutive words.
+constexpr int kLS = 32;
+
+// All contributions of one edge.  Xs[i*kLS]: the member values; Pre: this
+// lane's column for Pre_2..Pre_{s-1}; ib/sb: its member ids / incidence slots.
 template <typename T, int W, bool BUF>
 __device__ __forceinline__ void edge_compute(const EdgeBucketArgs &b, const EdgeOutArgs &o, const T *Xs, T *Pre,
-                                             const int32_t *ib, const int32_t *sb, int BS, int s) {
+                                             const int32_t *ib, const int32_t *sb, int s) {
     T S = T(0);
-    for (int i = 0; i < s; ++i) S += Arith<T>::absv(Xs[i * BS]);
+    for (int i = 0; i < s; ++i) S += Arith<T>::absv(Xs[i * kLS]);
     const int p = scale_exponent<T>(S, b.target);
     const T g = Arith<T>::pow2(p);
     const int32_t *ob = BUF ? sb : ib;  // where each member's result goes
+    const EdgeScale<T> sc = edge_scale(b, o, p, T(0));
+    int nbad = 0;
+    auto emit = [&](int q, T val, T xhat) {
+        const int t = ob[q * kLS];
+        if (sc.fast) emit_fast<T, BUF>(o, t, val, sc.mult, nbad);
+        else emit_value<T, BUF>(b, o, t, t, val, p, xhat);
+    };
 
     // forward: P = Pre_2, then Pre_3 .. Pre_s (windows Pre_2..Pre_{s-1} kept in shared memory)
     T P[W];
     power_table<T, W>(Xs[0] * g, P);
     for (int i = 1; i <= s - 2; ++i) {
+        T *slot = Pre + (i - 1) * W * kLS;
 #pragma unroll
-        for (int j = 0; j < W; ++j) Pre[((i - 1) * W + j) * BS] = P[j];
+        for (int j = 0; j < W; ++j) slot[j * kLS] = P[j];
         T xk[W];
-        ratio_table<T, W>(Xs[i * BS] * g, xk);
+        ratio_table<T, W>(Xs[i * kLS] * g, xk);
         toeplitz_horner<T, W>(P, xk);
     }
     // P = Pre_s.  backward: Q = Suf_{s-1} = Ebar(x_{v_s})
     T Q[W];
-    const T xs_last = Xs[(s - 1) * BS] * g;
+    const T xs_last = Xs[(s - 1) * kLS] * g;
     power_table<T, W>(xs_last, Q);
     T F = T(0);
 #pragma unroll
     for (int j = 0; j <= W - 2; ++j) F = Arith<T>::fma_(P[j], Q[W - 2 - j], F);
-    {
-        const int t = ob[(s - 1) * BS];
-        emit_value<T, BUF>(b, o, t, t, F + P[W - 1], p, xs_last);
-    }
+    emit(s - 1, F + P[W - 1], xs_last);
     T top = T(0);
     for (int q = s - 2; q >= 1; --q) {
         // Q = Suf_{q+1}; Pre_{q+1} sits in slot q-1
+        const T *slot = Pre + (q - 1) * W * kLS;
         T D = T(0);
 #pragma unroll
-        for (int j = 0; j < W; ++j) D = Arith<T>::fma_(Pre[((q - 1) * W + j) * BS], Q[W - 1 - j], D);
-        const T xq = Xs[q * BS] * g;
-        const int t = ob[q * BS];
-        emit_value<T, BUF>(b, o, t, t, F + D, p, xq);
+        for (int j = 0; j < W; ++j) D = Arith<T>::fma_(slot[j * kLS], Q[W - 1 - j], D);
+        const T xq = Xs[q * kLS] * g;
+        emit(q, F + D, xq);
         T xk[W];
         ratio_table<T, W>(xq, xk);
         if (q >= 2) toeplitz_horner<T, W>(Q, xk);
         else top = top_horner<T, W>(Q, xk);
     }
     T D1 = (s == 2) ? Q[W - 1] : top;
-    const int t0 = ob[0];
-    emit_value<T, BUF>(b, o, t0, t0, F + D1, p, Xs[0] * g);
+    emit(0, F + D1, Xs[0] * g);
+    if (nbad && o.range_events) atomicAdd(o.range_events, (unsigned long long)nbad);
 }
 
-// Shared memory per thread, interleaved across the block (element k of thread t
-// at k * blockDim + t): Xb[2][s] and Pre[(s-2) W] of T, then Ib[3][s] member ids
-// and Sb[3][s] incidence slots (int32).
+// Shared memory per lane: Xb[2][s] and Pre[(s-2) W] of T, then Ib[3][s] member
+// ids and Sb[3][s] incidence slots (int32); 4-byte words.
 template <typename T>
 __host__ __device__ constexpr size_t thread_smem_words(int s, int W) {
     return (size_t)(2 * s + (s > 2 ? (s - 2) * W : 0)) * sizeof(T) / 4 + (size_t)6 * s;
@@ -327,14 +389,15 @@ __global__ void __launch_bounds__(256) edge_thread_kernel(EdgeBucketArgs b, cons
     if (o.skip && *o.skip) return;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int BS = blockDim.x;
-    const int tid = threadIdx.x;
+    const int tid = threadIdx.x, lane = tid & 31;
     const int s = b.s;
-    T *tb = reinterpret_cast<T *>(smem_raw);
-    T *xc = tb + tid;                     // X of the edge being computed
-    T *xn = tb + (size_t)s * BS + tid;    // X of the next edge (in flight)
-    T *Pre = tb + (size_t)2 * s * BS + tid;
-    int32_t *ibase = reinterpret_cast<int32_t *>(tb + (size_t)(2 * s + (s > 2 ? (s - 2) * W : 0)) * BS) + tid;
-    const size_t ring = (size_t)s * BS;
+    const size_t words = thread_smem_words<T>(s, W);
+    T *wb = reinterpret_cast<T *>(smem_raw + (size_t)(tid >> 5) * words * 4 * kLS);  // this warp's region
+    T *xc = wb + lane;                   // X of the edge being computed
+    T *xn = xc + s * kLS;                // X of the next edge (in flight)
+    T *Pre = xc + 2 * s * kLS;
+    int32_t *ibase = reinterpret_cast<int32_t *>(wb + (2 * s + (s > 2 ? (s - 2) * W : 0)) * kLS) + lane;
+    const int ring = s * kLS;
     // ring slots (ids; the slots array sits 3 rings further): current, next, after next
     int32_t *r0 = ibase, *r1 = ibase + ring, *r2 = ibase + 2 * ring;
     const int64_t stride = (int64_t)gridDim.x * BS;
@@ -349,13 +412,13 @@ __global__ void __launch_bounds__(256) edge_thread_kernel(EdgeBucketArgs b, cons
         for (int i = 0; i < s; ++i) {
             cp_async<4>(d, gi);
             if (BUF) cp_async<4>(d + 3 * ring, gs);
-            d += BS;
+            d += kLS;
             gi += ld;
             gs += ld;
         }
     };
     auto issue_x = [&](const int32_t *src, T *xb) {
-        for (int i = 0; i < s; ++i) cp_async<(int)sizeof(T)>(xb + (size_t)i * BS, x + src[(size_t)i * BS]);
+        for (int i = 0; i < s; ++i) cp_async<(int)sizeof(T)>(xb + i * kLS, x + src[i * kLS]);
     };
 
     issue_ids(gid, gsl, r0);
@@ -369,7 +432,7 @@ __global__ void __launch_bounds__(256) edge_thread_kernel(EdgeBucketArgs b, cons
         if (e + stride < b.m) issue_x(r1, xn);
         if (e + 2 * stride < b.m) issue_ids(gid + 2 * stride, gsl + 2 * stride, r2);
         cp_async_commit();
-        edge_compute<T, W, BUF>(b, o, xc, Pre, r0, r0 + 3 * ring, BS, s);
+        edge_compute<T, W, BUF>(b, o, xc, Pre, r0, r0 + 3 * ring, s);
         gid += stride;
         gsl += stride;
         int32_t *t = r0;
@@ -381,6 +444,117 @@ __global__ void __launch_bounds__(256) edge_thread_kernel(EdgeBucketArgs b, cons
         xn = tx;
     }
     cp_async_wait_all();
+}
+
+// Size-2 edges.  With P = Ebar(x_{v_1}) and Q = Ebar(x_{v_2}) on degrees 1..W
+// (W = N - 1), F = [t^(N-1)] P Q = sum_{j=0}^{W-2} P[j] Q[W-2-j], and the two
+// contributions are K (F + P[W-1]) for v_2 and K (F + Q[W-1]) for v_1 -- the
+// general kernel's arithmetic at s = 2, in the same order.  The bucket moves
+// 32 bytes per edge for about 5 W flops, so this variant keeps only Q in
+// registers (P runs as a scalar), reads ids, slots and x with plain coalesced
+// or L2 loads and no shared memory, and keeps the loads of kPairEdges edges
+// per thread in flight together.
+constexpr int kPairEdges = 4;
+
+template <typename T, int W, bool BUF>
+__global__ void __launch_bounds__(256, 4) edge_pair_kernel(EdgeBucketArgs b, const T *__restrict__ x, EdgeOutArgs o) {
+    if (o.skip && *o.skip) return;
+    constexpr int E = kPairEdges;
+    const int64_t span = (int64_t)blockDim.x * E;
+    const int64_t stride = (int64_t)gridDim.x * span;
+    int nbad = 0;
+    for (int64_t e0 = (int64_t)blockIdx.x * span + threadIdx.x; e0 < b.m; e0 += stride) {
+        int v0[E], v1[E], t0[E], t1[E];
+        T X0[E], X1[E];
+#pragma unroll
+        for (int k = 0; k < E; ++k) {
+            const int64_t e = e0 + (int64_t)k * blockDim.x;
+            const bool in = e < b.m;
+            v0[k] = in ? __ldg(b.ids + e) : 0;
+            v1[k] = in ? __ldg(b.ids + b.ld + e) : 0;
+            t0[k] = BUF ? (in ? __ldg(b.slot + e) : 0) : v0[k];
+            t1[k] = BUF ? (in ? __ldg(b.slot + b.ld + e) : 0) : v1[k];
+        }
+#pragma unroll
+        for (int k = 0; k < E; ++k) {
+            X0[k] = __ldg(x + v0[k]);
+            X1[k] = __ldg(x + v1[k]);
+        }
+#pragma unroll
+        for (int k = 0; k < E; ++k) {
+            if (e0 + (int64_t)k * blockDim.x >= b.m) break;
+            const int p = scale_exponent<T>(Arith<T>::absv(X0[k]) + Arith<T>::absv(X1[k]), b.target);
+            const T g = Arith<T>::pow2(p);
+            const T a0 = X0[k] * g, a1 = X1[k] * g;
+            T Q[W];
+            power_table<T, W>(a1, Q);
+            T P = a0, F = T(0);
+#pragma unroll
+            for (int j = 0; j <= W - 2; ++j) {
+                F = Arith<T>::fma_(P, Q[W - 2 - j], F);
+                P = P * (a0 * (T(1) / T(j + 2)));
+            }
+            const EdgeScale<T> sc = edge_scale(b, o, p, T(0));
+            if (sc.fast) {
+                emit_fast<T, BUF>(o, t1[k], F + P, sc.mult, nbad);
+                emit_fast<T, BUF>(o, t0[k], F + Q[W - 1], sc.mult, nbad);
+            } else {
+                emit_value<T, BUF>(b, o, t1[k], t1[k], F + P, p, a1);
+                emit_value<T, BUF>(b, o, t0[k], t0[k], F + Q[W - 1], p, a0);
+            }
+        }
+    }
+    if (nbad && o.range_events) atomicAdd(o.range_events, (unsigned long long)nbad);
+}
+
+// --------------------------------------------- fused launch of small buckets --
+
+// Shared memory per lane of the one-edge-per-thread tail kernel: X[s] and
+// Pre[(s-2) W] of T, then ids[s] and slots[s] (int32); edge_tail_smem_words in
+// s3_kernels.h counts its 4-byte words.  Every warp's region holds lane_words
+// words per lane (the largest need of the launch's buckets).
+template <typename T, int W, bool BUF>
+__device__ __forceinline__ void tail_edge(const EdgeBucketArgs &b, const T *__restrict__ x, const EdgeOutArgs &o,
+                                          int64_t e, unsigned char *smem_raw, int lane_words) {
+    const int tid = threadIdx.x, lane = tid & 31, s = b.s;
+    T *wb = reinterpret_cast<T *>(smem_raw + (size_t)(tid >> 5) * lane_words * 4 * kLS);
+    T *xs = wb + lane;
+    T *Pre = xs + s * kLS;
+    int32_t *ib = reinterpret_cast<int32_t *>(wb + (s + (s > 2 ? (s - 2) * W : 0)) * kLS) + lane;
+    int32_t *sb = ib + s * kLS;
+    for (int i = 0; i < s; ++i) {
+        cp_async<4>(ib + i * kLS, b.ids + (int64_t)i * b.ld + e);
+        if (BUF) cp_async<4>(sb + i * kLS, b.slot + (int64_t)i * b.ld + e);
+    }
+    cp_async_commit();
+    cp_async_wait_all();
+    for (int i = 0; i < s; ++i) cp_async<(int)sizeof(T)>(xs + i * kLS, x + ib[i * kLS]);
+    cp_async_commit();
+    cp_async_wait_all();
+    edge_compute<T, W, BUF>(b, o, xs, Pre, ib, sb, s);
+}
+
+// All small buckets of a call in one launch: block ranges of the grid map to
+// buckets (TailEntry::block0 ascending), one edge per thread.  Buckets with few
+// edges are bound by the latency of one edge's load -> gather -> compute chain,
+// so one launch for all of them pays that latency once instead of per bucket.
+template <typename T, bool BUF>
+__global__ void __launch_bounds__(128) edge_tail_kernel(const TailEntry *__restrict__ tab, int ntab, int lane_words,
+                                                        const T *__restrict__ x, EdgeOutArgs o) {
+    if (o.skip && *o.skip) return;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    int k = 0;
+    while (k + 1 < ntab && tab[k + 1].block0 <= (int64_t)blockIdx.x) ++k;
+    const EdgeBucketArgs b = tab[k].b;
+    const int64_t e = ((int64_t)blockIdx.x - tab[k].block0) * blockDim.x + threadIdx.x;
+    if (e >= b.m) return;
+    switch (tab[k].W) {
+#define S3_TAIL_CASE(w) \
+    case w: tail_edge<T, w, BUF>(b, x, o, e, smem_raw, lane_words); break;
+        S3_W_CASES(S3_TAIL_CASE)
+#undef S3_TAIL_CASE
+        default: break;
+    }
 }
 
 // Size-1 edges: c(e, v) = x_v^(N-1) (K(1,N) [t^(N-1)] e^(x t) with K(1,N) = (N-1)!).
@@ -561,7 +735,7 @@ __global__ void __launch_bounds__(128) edge_warp_kernel(EdgeBucketArgs b, const 
 
 namespace s3 {
 
-constexpr size_t kSmemCap = 96 * 1024;        // per block, thread-per-edge kernel
+constexpr size_t kSmemCap = kEdgeSmemCap;     // per block, thread-per-edge kernels
 constexpr size_t kSmemCapWarp = 200 * 1024;   // per block, warp-per-edge kernel
 constexpr int kMaxThreadW = 32;
 
@@ -604,10 +778,6 @@ cudaError_t prepare_thread_w() {
                                 (int)kSmemCap);
 }
 
-#define S3_W_CASES(M) \
-    M(1) M(2) M(3) M(4) M(5) M(6) M(7) M(8) M(9) M(10) M(11) M(12) M(13) M(14) M(15) M(16) \
-    M(17) M(18) M(19) M(20) M(21) M(22) M(23) M(24) M(25) M(26) M(27) M(28) M(29) M(30) M(31) M(32)
-
 template <typename T>
 cudaError_t prepare_edge_kernels_t() {
     cudaError_t err = cudaSuccess;
@@ -616,7 +786,59 @@ cudaError_t prepare_edge_kernels_t() {
 #undef S3_PREP
     if (err == cudaSuccess)
         err = cudaFuncSetAttribute(edge_warp_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemCapWarp);
+    if (err == cudaSuccess)
+        err = cudaFuncSetAttribute(edge_tail_kernel<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemCap);
+    if (err == cudaSuccess)
+        err = cudaFuncSetAttribute(edge_tail_kernel<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemCap);
     return err;
+}
+
+// Blocks of a grid-stride kernel that fill the device once (occupancy x SMs) for a
+// fixed block size and no dynamic shared memory, queried once per kernel.
+template <auto Kernel, int BS>
+int64_t full_grid() {
+    static int sms = 0, per_sm = 0;
+    if (sms == 0) {
+        int dev = 0, n = 0, k = 0;
+        cudaGetDevice(&dev);
+        if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0) n = 148;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&k, Kernel, BS, 0) != cudaSuccess || k <= 0) {
+            cudaGetLastError();
+            k = 1;
+        }
+        per_sm = k;
+        sms = n;
+    }
+    return (int64_t)sms * per_sm;
+}
+
+template <typename T, int W>
+cudaError_t launch_pair_w(const EdgeBucketArgs &b, const T *x, const EdgeOutArgs &o, cudaStream_t st) {
+    constexpr int bs = 256;
+    const int64_t need = (b.m + bs - 1) / bs;
+    if (o.mode == kOutBuffer) {
+        const int64_t grid = std::min<int64_t>(need, full_grid<edge_pair_kernel<T, W, true>, bs>());
+        edge_pair_kernel<T, W, true><<<(unsigned)grid, bs, 0, st>>>(b, x, o);
+    } else {
+        const int64_t grid = std::min<int64_t>(need, full_grid<edge_pair_kernel<T, W, false>, bs>());
+        edge_pair_kernel<T, W, false><<<(unsigned)grid, bs, 0, st>>>(b, x, o);
+    }
+    return cudaGetLastError();
+}
+
+// The fused launch of the small buckets listed in tab (device memory, ntab entries,
+// nblocks blocks of bs threads in total, smem bytes of dynamic shared memory).
+template <typename T>
+cudaError_t launch_edge_tail_t(const TailEntry *tab, int ntab, int64_t nblocks, int bs, size_t smem, const T *x,
+                               const EdgeOutArgs &o, cudaStream_t st) {
+    if (ntab <= 0 || nblocks <= 0) return cudaSuccess;
+    if (smem > kSmemCap || nblocks > INT32_MAX) return cudaErrorInvalidConfiguration;
+    const int lane_words = (int)(smem / 4 / (size_t)bs);
+    if (o.mode == kOutBuffer)
+        edge_tail_kernel<T, true><<<(unsigned)nblocks, bs, smem, st>>>(tab, ntab, lane_words, x, o);
+    else
+        edge_tail_kernel<T, false><<<(unsigned)nblocks, bs, smem, st>>>(tab, ntab, lane_words, x, o);
+    return cudaGetLastError();
 }
 
 // Threads per block for the thread-per-edge kernel so that the block's shared
@@ -641,6 +863,15 @@ cudaError_t launch_edge_bucket_t(const EdgeBucketArgs &b, const T *x, const Edge
     const int W = b.N - b.s + 1;
     if (thread_max_w <= 0 || thread_max_w > kMaxThreadW) thread_max_w = kMaxThreadW;
     if (block_threads <= 0) block_threads = 128;
+    if (b.s == 2 && W <= thread_max_w) {
+        switch (W) {
+#define S3_CASE(w) \
+    case w: return launch_pair_w<T, w>(b, x, o, st);
+            S3_W_CASES(S3_CASE)
+#undef S3_CASE
+            default: break;
+        }
+    }
     if (W <= thread_max_w) {
         int bs = thread_block_size<T>(b.s, W, block_threads);
         if (bs > 0) {

@@ -60,6 +60,28 @@ def test_powerlaw_medium_rank25():
     check(hg, x, reduces=(0,), thread_max_w=8)
 
 
+@pytest.mark.parametrize("small", [-1, 0, 1 << 30])
+def test_small_bucket_fusion(small):
+    # -1: one launch per bucket (pipelined kernels, size-2 kernel); 0: default
+    # threshold; 2^30: every thread-per-edge bucket of size >= 2 in the fused launch
+    hg = s3synth.config_powerlaw(n=20000, m=100000, rank=25, seed=13)
+    x = s3synth.x_uniform(hg.n, 0.5, 1.5, 13)
+    check(hg, x, small_bucket_edges=small)
+    check(hg, x, reduces=(0,), small_bucket_edges=small, block_threads=64, streams=1)
+    hg = s3synth.config_small(seed=2)
+    check(hg, s3synth.x_uniform(hg.n, 0.0, 1.0, 2), small_bucket_edges=small)
+
+
+def test_size_two_edges_all_ranks():
+    # the size-2 kernel for every window W = N - 1 = 1..32 (and the warp path beyond)
+    rng = np.random.default_rng(4)
+    edges = [tuple(rng.choice(400, size=2, replace=False)) for _ in range(3000)]
+    hg = s3synth.from_edges(400, edges)
+    x = s3synth.x_uniform(hg.n, 0.1, 1.4, 4)
+    for N in (2, 3, 9, 25, 33, 34, 40):
+        check(hg, x, N=N, reduces=(0, 1), small_bucket_edges=-1)
+
+
 def test_large_rank_100():
     hg = s3synth.config_large_rank(n=3000, m=4000, rank=100, seed=12)
     x = s3synth.x_uniform(hg.n, 0.5, 1.5, 12)
