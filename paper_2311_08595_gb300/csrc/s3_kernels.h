@@ -63,6 +63,15 @@ inline size_t edge_tail_smem_words(int s, int W, int value_bytes) {
     return (size_t)(s + (s > 2 ? (s - 2) * W : 0)) * (size_t)value_bytes / 4 + (size_t)2 * s;
 }
 constexpr size_t kEdgeSmemCap = 96 * 1024;   // dynamic shared memory per block of the thread kernels
+// Buckets with wide windows: eight lanes per edge (s3_group.cuh; FP32 only).  Sets
+// *launched = 1 if it launched, 0 if it did not (FP64, or edges too large for the
+// kernel's shared memory): the caller then uses one warp per edge.
+cudaError_t launch_edge_group(const EdgeBucketArgs &b, const float *x, const EdgeOutArgs &o, int W, cudaStream_t st,
+                              int *launched);
+cudaError_t launch_edge_group(const EdgeBucketArgs &b, const double *x, const EdgeOutArgs &o, int W, cudaStream_t st,
+                              int *launched);
+cudaError_t prepare_edge_group(float);
+cudaError_t prepare_edge_group(double);
 // One-time per-device set-up (shared-memory limits of the kernels).
 cudaError_t prepare_edge_kernels_f32();
 cudaError_t prepare_edge_kernels_f64();

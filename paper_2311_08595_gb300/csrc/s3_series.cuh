@@ -786,6 +786,7 @@ cudaError_t prepare_edge_kernels_t() {
 #undef S3_PREP
     if (err == cudaSuccess)
         err = cudaFuncSetAttribute(edge_warp_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemCapWarp);
+if (err == cudaSuccess) err = prepare_edge_group(T(0));
     if (err == cudaSuccess)
         err = cudaFuncSetAttribute(edge_tail_kernel<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemCap);
     if (err == cudaSuccess)
@@ -883,6 +884,12 @@ cudaError_t launch_edge_bucket_t(const EdgeBucketArgs &b, const T *x, const Edge
                 default: break;
             }
         }
+    }
+    // wide windows: four lanes per edge (s3_group.cuh) when eight edges fit a warp's shared memory
+    {
+        int launched = 0;
+        cudaError_t e = launch_edge_group(b, x, o, W, st, &launched);
+        if (e != cudaSuccess || launched) return e;
     }
     // one warp per edge
     int64_t per_warp = warp_smem_elems(b.s, W);
