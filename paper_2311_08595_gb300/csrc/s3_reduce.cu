@@ -94,8 +94,9 @@ __device__ __forceinline__ void load_partial(const void *p, int64_t i, AccD &a) 
 
 constexpr int kRedThreads = 256;
 
-// Eight loads in flight per thread (then added in order): the kernel is bound
-// by memory latency, not by its few flops.
+// Eight loads in flight per thread, predicated at the end of a segment (a
+// missing value is 0, and adding 0 leaves a sum unchanged), then added in
+// order: the kernel is bound by memory latency, not by its few flops.
 constexpr int kRedUnroll = 8;
 
 // Blocks [0, n_pieces): one hub piece each (the longest-running blocks start
@@ -116,15 +117,13 @@ __global__ void __launch_bounds__(kRedThreads) reduce_kernel(ReduceArgs r, const
         const T *p = buf + r.piece_start[pc];
         const int len = r.piece_len[pc];
         A a;
-        int k = tid;
-        for (; k + (U - 1) * kRedThreads < len; k += U * kRedThreads) {
+        for (int k = tid; k < len; k += U * kRedThreads) {
             T v[U];
 #pragma unroll
-            for (int u = 0; u < U; ++u) v[u] = p[k + u * kRedThreads];
+            for (int u = 0; u < U; ++u) v[u] = k + u * kRedThreads < len ? p[k + u * kRedThreads] : T(0);
 #pragma unroll
             for (int u = 0; u < U; ++u) a.add(v[u]);
         }
-        for (; k < len; k += kRedThreads) a.add(p[k]);
         a = warp_reduce(a);
         if (lane == 0) part[tid >> 5] = a;
         __syncthreads();
@@ -157,15 +156,13 @@ __global__ void __launch_bounds__(kRedThreads) reduce_kernel(ReduceArgs r, const
         const T *p = buf + r.med_off[i];
         const int len = r.med_len[i];
         A a;
-        int k = lane;
-        for (; k + (U - 1) * 32 < len; k += U * 32) {
+        for (int k = lane; k < len; k += U * 32) {
             T w[U];
 #pragma unroll
-            for (int u = 0; u < U; ++u) w[u] = p[k + u * 32];
+            for (int u = 0; u < U; ++u) w[u] = k + u * 32 < len ? p[k + u * 32] : T(0);
 #pragma unroll
-            for (int u = 0; u < U; ++u) a.add(w[u]);
+            for (int u = 0; u < U; ++u) a.add(w[u]);  // adding 0 leaves the sum unchanged
         }
-        for (; k < len; k += 32) a.add(p[k]);
         a = warp_reduce(a);
         if (lane == 0) y[v] = (T)a.value();
     } else if (bid < r.n_pieces + nb_med + nb_med8) {
@@ -176,15 +173,13 @@ __global__ void __launch_bounds__(kRedThreads) reduce_kernel(ReduceArgs r, const
         const T *p = has ? buf + r.med8_off[i] : buf;
         const int len = has ? r.med8_len[i] : 0;
         A a;
-        int k = sl;
-        for (; k + (U - 1) * 8 < len; k += U * 8) {
+        for (int k = sl; k < len; k += U * 8) {
             T w[U];
 #pragma unroll
-            for (int u = 0; u < U; ++u) w[u] = p[k + u * 8];
+            for (int u = 0; u < U; ++u) w[u] = k + u * 8 < len ? p[k + u * 8] : T(0);
 #pragma unroll
             for (int u = 0; u < U; ++u) a.add(w[u]);
         }
-        for (; k < len; k += 8) a.add(p[k]);
         a = group8_reduce(a);
         if (has && sl == 0) y[r.med8_nodes[i]] = (T)a.value();
     } else {
@@ -194,15 +189,13 @@ __global__ void __launch_bounds__(kRedThreads) reduce_kernel(ReduceArgs r, const
         const int d = r.grp_deg[gi * 32 + lane];
         const T *p = buf + r.grp_off[gi] + lane;
         A a;
-        int k = 0;
-        for (; k + U <= d; k += U) {  // U coalesced rows in flight, added in order
+        for (int k = 0; k < d; k += U) {  // U coalesced rows in flight, added in order
             T w[U];
 #pragma unroll
-            for (int u = 0; u < U; ++u) w[u] = p[32 * (k + u)];
+            for (int u = 0; u < U; ++u) w[u] = k + u < d ? p[32 * (k + u)] : T(0);
 #pragma unroll
             for (int u = 0; u < U; ++u) a.add(w[u]);
         }
-        for (; k < d; ++k) a.add(p[32 * k]);
         if (node >= 0) y[node] = (T)a.value();
     }
 }

@@ -786,7 +786,7 @@ cudaError_t prepare_edge_kernels_t() {
 #undef S3_PREP
     if (err == cudaSuccess)
         err = cudaFuncSetAttribute(edge_warp_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemCapWarp);
-if (err == cudaSuccess) err = prepare_edge_group(T(0));
+    if (err == cudaSuccess) err = prepare_edge_group(T(0));
     if (err == cudaSuccess)
         err = cudaFuncSetAttribute(edge_tail_kernel<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemCap);
     if (err == cudaSuccess)
