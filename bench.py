@@ -132,6 +132,18 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def csrc_digest():
+    """sha256 over the library's kernel and host sources (names and contents)."""
+    import glob
+    import hashlib
+    h = hashlib.sha256()
+    for p in sorted(glob.glob(os.path.join(ROOT, "paper_2311_08595_gb300", "csrc", "*"))):
+        h.update(os.path.basename(p).encode())
+        with open(p, "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()
+
+
 def dist_env():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -267,11 +279,15 @@ def run_gpu(args):
     fp32_peak_tflops = 152 * 128 * 2 * sm_max * 1e6 / 1e12
     achieved_tflops = flops / (edge_ms * 1e-3) / 1e12
     bytes_call = hbm_bytes(nnz, n, 0)
+    # DRAM traffic of the edge kernels of one call, from the committed ncu capture -- only while
+    # the kernel sources are the ones it was taken with
     traffic = None
     tp = os.path.join(ROOT, "profiles", "edge_kernels_traffic.json")
     if os.path.exists(tp):
         try:
-            traffic = json.load(open(tp)).get("bytes_per_call")
+            tj = json.load(open(tp))
+            if tj.get("csrc_digest") == csrc_digest():
+                traffic = tj.get("bytes_per_call")
         except Exception:
             traffic = None
     out = {
