@@ -58,7 +58,15 @@ typedef enum {
     S3_ENOTSUP = 7    /* configuration not supported by this build */
 } s3_status;
 
-typedef enum { S3_F32 = 0, S3_F64 = 1 } s3_dtype;
+/*
+ * Arithmetic of a call.  S3_F32 / S3_F64: x, y and the series in that type.
+ * S3_DF64: x and y are FP64 (double); the series of the edges run in
+ * double-float -- each value an unevaluated sum of two FP32 numbers, about 44
+ * significant bits -- on the FP32 units (GB300 runs FP32 many times faster than
+ * FP64).  Size-1 edges, windows N-|e|+1 wider than 24 and the CCSS layout use
+ * FP64.  Relative error per node is of order 1e-13 for non-negative x.
+ */
+typedef enum { S3_F32 = 0, S3_F64 = 1, S3_DF64 = 2 } s3_dtype;
 
 typedef enum {
     /* y_v is summed node by node from a per-(edge, node) buffer laid out in
@@ -203,8 +211,11 @@ typedef struct {
     double tol;            /* stop when (lambda_max - lambda_min)/lambda_min < tol (Algorithm 1) */
     int32_t max_iter;      /* passes through the repeat body; <= 0 = 10000 */
     int32_t precision;     /* 0 = FP64 throughout; 1 = FP32 series until the gap is below
-                              switch_tol (or stops shrinking), then FP64 to tol */
-    double switch_tol;     /* FP32 -> FP64 hand-over gap for precision 1; <= 0 = 1e-5 */
+                              switch_tol (or stops shrinking), then FP64 to tol; 2 = as 1 with
+                              double-float series (S3_DF64) instead of FP64 after the switch;
+                              3 = double-float series throughout.  Norms, roots, ratios and
+                              the bracket are FP64 in every mode. */
+    double switch_tol;     /* FP32 -> FP64 hand-over gap for precision 1 and 2; <= 0 = 1e-5 */
     int32_t check_every;   /* iterations per captured CUDA graph between host checks; <= 0 = 8 */
     int32_t reserved[7];
 } s3_nqz_options;

@@ -20,7 +20,7 @@ import ctypes
 import numpy as np
 
 from . import _lib
-from ._lib import (S3_F32, S3_F64, S3_LAYOUT_CCSS, S3_LAYOUT_EDGE, S3_REDUCE_ATOMIC,  # noqa: F401
+from ._lib import (S3_DF64, S3_F32, S3_F64, S3_LAYOUT_CCSS, S3_LAYOUT_EDGE, S3_REDUCE_ATOMIC,  # noqa: F401
                    S3_REDUCE_SEGMENTED, S3Error, check, load, ptr)
 
 __all__ = [
@@ -108,13 +108,14 @@ def s3_graph_query(g):
     return _info_dict(info)
 
 
-def _dtype_code(t):
+def _dtype_code(t, df=False):
+    """S3_F32 / S3_F64 from the tensor dtype; df=True: FP64 tensors, double-float series (S3_DF64)."""
     import torch
-    if t.dtype == torch.float32:
+    if t.dtype == torch.float32 and not df:
         return S3_F32
     if t.dtype == torch.float64:
-        return S3_F64
-    raise TypeError("x must be float32 or float64")
+        return S3_DF64 if df else S3_F64
+    raise TypeError("x must be float32 or float64 (float64 for df=True)")
 
 
 def _stream(stream):
@@ -129,20 +130,21 @@ def _check_vec(g, t, name):
         raise ValueError(f"{name} must be a contiguous CUDA tensor of {g.n} elements")
 
 
-def s3_sttsvc(g, x, y, stream=None):
-    """y = B x^(N-1) on the device (x, y: CUDA tensors of the same float dtype)."""
+def s3_sttsvc(g, x, y, stream=None, df=False):
+    """y = B x^(N-1) on the device (x, y: CUDA tensors of the same float dtype; df=True with
+    float64 tensors runs the series in double-float, S3_DF64)."""
     _check_vec(g, x, "x")
     _check_vec(g, y, "y")
     if x.dtype != y.dtype:
         raise TypeError("x and y must have the same dtype")
-    check(load().s3_sttsvc(g.handle, _dtype_code(x), ptr(x), ptr(y), _stream(stream)))
+    check(load().s3_sttsvc(g.handle, _dtype_code(x, df), ptr(x), ptr(y), _stream(stream)))
     return y
 
 
-def s3_sttsvc_layout(g, layout, x, y, stream=None):
+def s3_sttsvc_layout(g, layout, x, y, stream=None, df=False):
     _check_vec(g, x, "x")
     _check_vec(g, y, "y")
-    check(load().s3_sttsvc_layout(g.handle, _dtype_code(x), int(layout), ptr(x), ptr(y), _stream(stream)))
+    check(load().s3_sttsvc_layout(g.handle, _dtype_code(x, df), int(layout), ptr(x), ptr(y), _stream(stream)))
     return y
 
 
@@ -158,12 +160,13 @@ def s3_sttsvc_host(g, x_host, y_host, stream=None):
     return y_host
 
 
-def s3_sttsvc_profile(g, x, y, stream=None):
+def s3_sttsvc_profile(g, x, y, stream=None, df=False):
     """One S^3TTVc call with device timings of its phases (synchronises); returns a dict."""
     _check_vec(g, x, "x")
     _check_vec(g, y, "y")
     prof = _lib.s3_profile()
-    check(load().s3_sttsvc_profile(g.handle, _dtype_code(x), ptr(x), ptr(y), ctypes.byref(prof), _stream(stream)))
+    check(load().s3_sttsvc_profile(g.handle, _dtype_code(x, df), ptr(x), ptr(y), ctypes.byref(prof),
+                                   _stream(stream)))
     return {"edge_ms": prof.edge_ms, "reduce_ms": prof.reduce_ms, "total_ms": prof.total_ms,
             "launches": prof.launches}
 

@@ -37,6 +37,7 @@ s3_status prepare_device(int dev) {
     if (done[dev]) return S3_OK;
     S3_CUDA(prepare_edge_kernels_f32());
     S3_CUDA(prepare_edge_kernels_f64());
+    S3_CUDA(prepare_edge_kernels_df());
     done[dev] = 1;
     return S3_OK;
 }
@@ -101,7 +102,9 @@ s3_status run_edges(s3_graph_s *g, s3_dtype dt, const void *x, void *y, int bias
         load[best] += cost;
         return g->aux[best];
     };
-    bool tail_done = g->n_tail == 0;
+    // small buckets share one launch (FP32, FP64); the double-float kernels launch per bucket
+    const bool fuse = dt != S3_DF64;
+    bool tail_done = !fuse || g->n_tail == 0;
     auto launch_tail = [&]() -> s3_status {
         tail_done = true;
         cudaStream_t ts = pick(g->tail_cost);
@@ -116,7 +119,7 @@ s3_status run_edges(s3_graph_s *g, s3_dtype dt, const void *x, void *y, int bias
     for (size_t r = 0; r < g->bucket_order.size(); ++r) {
         const size_t k = g->bucket_order[r];
         const HostBucket &hb = g->buckets[k];
-        if (hb.m <= 0 || g->in_tail[k]) continue;
+        if (hb.m <= 0 || (fuse && g->in_tail[k])) continue;
         if (!tail_done && g->tail_cost >= g->bucket_cost[k]) {
             s3_status ts = launch_tail();
             if (ts != S3_OK) return ts;
@@ -133,9 +136,10 @@ s3_status run_edges(s3_graph_s *g, s3_dtype dt, const void *x, void *y, int bias
         b.Km = g->Km[k];
         b.Ke = g->Ke[k];
         cudaStream_t bs = pick(g->bucket_cost[k]);
-        cudaError_t e = dt == S3_F32
-                            ? launch_edge_bucket_f32(b, (const float *)x, o, g->opt.thread_max_w, g->opt.block_threads, bs)
-                            : launch_edge_bucket_f64(b, (const double *)x, o, g->opt.thread_max_w, g->opt.block_threads, bs);
+        const int tmw = g->opt.thread_max_w, bth = g->opt.block_threads;
+        cudaError_t e = dt == S3_F32   ? launch_edge_bucket_f32(b, (const float *)x, o, tmw, bth, bs)
+                        : dt == S3_F64 ? launch_edge_bucket_f64(b, (const double *)x, o, tmw, bth, bs)
+                                       : launch_edge_bucket_df(b, (const double *)x, o, tmw, bth, bs);
         if (e != cudaSuccess) return cuda_fail(e, "edge kernel launch");
         ++launches;
     }
@@ -372,7 +376,7 @@ s3_status s3_graph_query(s3_graph_t g, s3_format_info *info) {
 
 s3_status s3_sttsvc_layout(s3_graph_t g, s3_dtype dt, int32_t layout, const void *x, void *y, void *stream) {
     if (!g) return fail(S3_EINVAL, "graph is NULL");
-    if (dt != S3_F32 && dt != S3_F64) return fail(S3_EINVAL, "bad dtype");
+    if (dt != S3_F32 && dt != S3_F64 && dt != S3_DF64) return fail(S3_EINVAL, "bad dtype");
     if (!x || !y) return fail(S3_EINVAL, "x or y is NULL");
     const size_t esz = dt == S3_F32 ? 4 : 8;
     const char *xb = (const char *)x, *yb = (const char *)y;
@@ -382,7 +386,7 @@ s3_status s3_sttsvc_layout(s3_graph_t g, s3_dtype dt, int32_t layout, const void
     if (layout == S3_LAYOUT_EDGE) return run_edges(g, dt, x, y, 0, nullptr, st);
     if (layout == S3_LAYOUT_CCSS) {
         if (!g->has_ccss) return fail(S3_EINVAL, "handle was built without the CCSS forest");
-        return run_ccss(g, dt, x, y, 0, nullptr, st);
+        return run_ccss(g, dt == S3_DF64 ? S3_F64 : dt, x, y, 0, nullptr, st);
     }
     return fail(S3_EINVAL, "bad layout");
 }
@@ -395,7 +399,7 @@ s3_status s3_sttsvc(s3_graph_t g, s3_dtype dt, const void *x, void *y, void *str
 s3_status s3_sttsvc_host(s3_graph_t g, s3_dtype dt, const void *x_host, void *y_host, void *stream) {
     if (!g) return fail(S3_EINVAL, "graph is NULL");
     if (!x_host || !y_host) return fail(S3_EINVAL, "x or y is NULL");
-    if (dt != S3_F32 && dt != S3_F64) return fail(S3_EINVAL, "bad dtype");
+    if (dt != S3_F32 && dt != S3_F64 && dt != S3_DF64) return fail(S3_EINVAL, "bad dtype");
     DeviceGuard guard(g->device);
     cudaStream_t st = (cudaStream_t)stream;
     const size_t bytes = (dt == S3_F32 ? 4 : 8) * (size_t)g->n;
@@ -409,7 +413,7 @@ s3_status s3_sttsvc_host(s3_graph_t g, s3_dtype dt, const void *x_host, void *y_
 
 s3_status s3_sttsvc_profile(s3_graph_t g, s3_dtype dt, const void *x, void *y, s3_profile *prof, void *stream) {
     if (!g || !prof) return fail(S3_EINVAL, "NULL argument");
-    if (dt != S3_F32 && dt != S3_F64) return fail(S3_EINVAL, "bad dtype");
+    if (dt != S3_F32 && dt != S3_F64 && dt != S3_DF64) return fail(S3_EINVAL, "bad dtype");
     if (!x || !y) return fail(S3_EINVAL, "x or y is NULL");
     if (g->opt.layout != S3_LAYOUT_EDGE) return fail(S3_ENOTSUP, "profiling covers the edge layout");
     DeviceGuard guard(g->device);

@@ -50,6 +50,10 @@ cudaError_t launch_edge_bucket_f32(const EdgeBucketArgs &b, const float *x, cons
                                    int thread_max_w, int block_threads, cudaStream_t st);
 cudaError_t launch_edge_bucket_f64(const EdgeBucketArgs &b, const double *x, const EdgeOutArgs &o,
                                    int thread_max_w, int block_threads, cudaStream_t st);
+// FP64 x and results, series in double-float (pairs of FP32); size-1 edges and windows
+// wider than 24 go to the FP64 kernels.  Small buckets are not fused for it.
+cudaError_t launch_edge_bucket_df(const EdgeBucketArgs &b, const double *x, const EdgeOutArgs &o,
+                                  int thread_max_w, int block_threads, cudaStream_t st);
 // Fused launch of small buckets: tab (device) lists ntab buckets by ascending
 // block0; nblocks blocks of bs threads; smem bytes of dynamic shared memory,
 // bs * the largest edge_tail_smem_words of the entries * 4.
@@ -75,6 +79,7 @@ cudaError_t prepare_edge_group(double);
 // One-time per-device set-up (shared-memory limits of the kernels).
 cudaError_t prepare_edge_kernels_f32();
 cudaError_t prepare_edge_kernels_f64();
+cudaError_t prepare_edge_kernels_df();
 
 // Deterministic segmented reduce of a node-sorted buffer into y.
 struct ReduceArgs {

@@ -227,8 +227,9 @@ s3_status nqz_step(s3_graph_s *g, const NqzBufs &b, s3_dtype tz, s3_dtype tc, do
         if (s != S3_OK) return s;
         nqz_ratio_kernel<float><<<kNqzBlocks, kNqzThreads, 0, st>>>(b.z32, b.x32, n, k, b.part_mm, b.flags);
     } else {
+        // tc: S3_F64 or S3_DF64 (FP64 vectors either way; the CCSS layout runs FP64)
         s = g->opt.layout == S3_LAYOUT_CCSS && g->has_ccss ? run_ccss(g, S3_F64, b.x64, b.z64, 1, b.flags, st)
-                                                            : run_edges(g, S3_F64, b.x64, b.z64, 1, b.flags, st);
+                                                            : run_edges(g, tc, b.x64, b.z64, 1, b.flags, st);
         if (s != S3_OK) return s;
         nqz_ratio_kernel<double><<<kNqzBlocks, kNqzThreads, 0, st>>>(b.z64, b.x64, n, k, b.part_mm, b.flags);
     }
@@ -267,6 +268,7 @@ s3_status s3_hcentrality(s3_graph_t g, const s3_nqz_options *opt_in, const doubl
     if (opt.check_every <= 0) opt.check_every = 8;
     if (opt.switch_tol <= 0) opt.switch_tol = 1e-5;
     if (!(opt.tol > 0)) return fail(S3_EINVAL, "tol must be > 0");
+    if (opt.precision < 0 || opt.precision > 3) return fail(S3_EINVAL, "precision must be in 0..3");
     if (g->N < 2) return fail(S3_EINVAL, "NQZ needs rank >= 2");
     DeviceGuard guard(g->device);
     cudaStream_t st = (cudaStream_t)stream;
@@ -313,8 +315,9 @@ s3_status s3_hcentrality(s3_graph_t g, const s3_nqz_options *opt_in, const doubl
 
     S3_CUDA(cudaMemsetAsync(b.flags, 0, 8 * sizeof(int32_t), st));
     // start vector y (Algorithm 1: 1/n) and z = TTSV1(y)
-    const bool fp32 = opt.precision == 1;
-    s3_dtype phase = fp32 ? S3_F32 : S3_F64;
+    const bool fp32 = opt.precision == 1 || opt.precision == 2;
+    const s3_dtype hi = opt.precision >= 2 ? S3_DF64 : S3_F64;  // series after the FP32 phase
+    s3_dtype phase = fp32 ? S3_F32 : hi;
     if (x0) {
         if (fp32) copy_cast_kernel<float><<<gb, 256, 0, st>>>(x0, b.x32, n);
         else copy_cast_kernel<double><<<gb, 256, 0, st>>>(x0, b.x64, n);
@@ -327,7 +330,7 @@ s3_status s3_hcentrality(s3_graph_t g, const s3_nqz_options *opt_in, const doubl
     auto ttsv = [&](s3_dtype dt) -> s3_status {
         if (dt == S3_F32)
             return ccss ? run_ccss(g, S3_F32, b.x32, b.z32, 1, b.flags, st) : run_edges(g, S3_F32, b.x32, b.z32, 1, b.flags, st);
-        return ccss ? run_ccss(g, S3_F64, b.x64, b.z64, 1, b.flags, st) : run_edges(g, S3_F64, b.x64, b.z64, 1, b.flags, st);
+        return ccss ? run_ccss(g, S3_F64, b.x64, b.z64, 1, b.flags, st) : run_edges(g, dt, b.x64, b.z64, 1, b.flags, st);
     };
     s = ttsv(phase);
     if (s != S3_OK) return s;
@@ -390,13 +393,13 @@ s3_status s3_hcentrality(s3_graph_t g, const s3_nqz_options *opt_in, const doubl
                 S3_CUDA(cudaMemcpyAsync(b.flags + F_DONE, &zero, sizeof(int32_t), cudaMemcpyHostToDevice, st));
                 S3_CUDA(cudaMemcpyAsync(b.flags + F_RANGE, &zero, sizeof(int32_t), cudaMemcpyHostToDevice, st));
                 S3_CUDA(cudaStreamSynchronize(st));
-                phase = S3_F64;
+                phase = hi;
                 switched = true;
                 if (flags[F_RANGE]) {
                     // the last FP32 z is unusable: redo z = TTSV1(x) in FP64 from the same x
-                    s = ttsv(S3_F64);
+                    s = ttsv(hi);
                     if (s != S3_OK) return s;
-                    last_z = S3_F64;
+                    last_z = hi;
                 }
                 continue;
             }

@@ -25,6 +25,7 @@
 #include <algorithm>
 #include <cfloat>
 #include <cstdint>
+#include <type_traits>
 
 #include "s3_kernels.h"
 
@@ -71,6 +72,70 @@ template <> struct Arith<double> {
     __device__ __forceinline__ static double huge() { return DBL_MAX; }
     __device__ __forceinline__ static double scale2(double v, int e) { return ldexp(v, e); }
     __device__ __forceinline__ static double fma_(double a, double b, double c) { return fma(a, b, c); }
+};
+
+// --------------------------------------------------------- double-float --
+
+// An unevaluated sum hi + lo of two FP32 numbers (|lo| <= ulp(hi)/2): about 44
+// bits of significand from FP32 instructions, with the error-free sum of
+// Knuth (TAOCP 4.2.2) and the FMA-based exact product (after Dekker, 1971).
+// Every operation uses the _rn intrinsics, which the compiler never fuses, so
+// the error-free transformations stay exact.  The series of an edge run in it
+// when S^3TTVc is called with S3_DF64: GB300 executes FP32 at many times its
+// FP64 rate, and the windows' values are all near 1 after the per-edge scaling.
+struct DF {
+    float hi, lo;
+};
+
+__device__ __forceinline__ DF df_fast_two_sum(float a, float b) {  // |a| >= |b| or a == 0
+    const float s = __fadd_rn(a, b);
+    return DF{s, __fsub_rn(b, __fsub_rn(s, a))};
+}
+__device__ __forceinline__ DF df_two_sum(float a, float b) {
+    const float s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    return DF{s, __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb))};
+}
+__device__ __forceinline__ DF operator+(DF a, DF b) {
+    const DF s = df_two_sum(a.hi, b.hi);
+    return df_fast_two_sum(s.hi, __fadd_rn(s.lo, __fadd_rn(a.lo, b.lo)));
+}
+__device__ __forceinline__ DF operator*(DF a, DF b) {
+    const float p = __fmul_rn(a.hi, b.hi);
+    float e = __fmaf_rn(a.hi, b.hi, -p);
+    e = __fmaf_rn(a.hi, b.lo, __fmaf_rn(a.lo, b.hi, e));
+    return df_fast_two_sum(p, e);
+}
+__device__ __forceinline__ DF df_from(double d) {
+    const float h = __double2float_rn(d);
+    return DF{h, __double2float_rn(d - (double)h)};
+}
+__device__ __forceinline__ double df_to(DF a) { return (double)a.hi + (double)a.lo; }
+
+template <> struct Arith<DF> {
+    __device__ __forceinline__ static DF fma_(DF a, DF b, DF c) { return a * b + c; }
+};
+
+// Value types of a kernel instance: T is the arithmetic of the series, In the
+// type of x (and of the member values in shared memory and the scaling), Out
+// the type of the results.
+template <typename T> struct Num {
+    using In = T;
+    using Out = T;
+    __device__ __forceinline__ static T cvt(In v) { return v; }
+    __device__ __forceinline__ static Out out(T v) { return v; }
+    __device__ __forceinline__ static T zero() { return T(0); }
+    __device__ __forceinline__ static T add(T a, T b) { return a + b; }
+    __device__ __forceinline__ static T recip(int k) { return T(1) / T(k); }
+};
+template <> struct Num<DF> {
+    using In = double;
+    using Out = double;
+    __device__ __forceinline__ static DF cvt(double v) { return df_from(v); }
+    __device__ __forceinline__ static double out(DF v) { return df_to(v); }
+    __device__ __forceinline__ static DF zero() { return DF{0.f, 0.f}; }
+    __device__ __forceinline__ static DF add(DF a, DF b) { return a + b; }
+    __device__ __forceinline__ static DF recip(int k) { return df_from(1.0 / (double)k); }
 };
 
 // p such that 2^p * S is within a factor 2 of target (integer exponent arithmetic only).
@@ -163,7 +228,7 @@ template <typename T, int W>
 __device__ __forceinline__ void power_table(T X, T (&a)[W]) {
     a[0] = X;
 #pragma unroll
-    for (int k = 1; k < W; ++k) a[k] = a[k - 1] * (X * (T(1) / T(k + 1)));
+    for (int k = 1; k < W; ++k) a[k] = a[k - 1] * (X * Num<T>::recip(k + 1));
 }
 
 // P <- P * Ebar(x) on the window (one degree up): P[j] = sum_{j' <= j} a[j-j'] P[j']
@@ -182,7 +247,7 @@ __device__ __forceinline__ void toeplitz_inplace(T (&P)[W], const T (&a)[W]) {
 template <typename T, int W>
 __device__ __forceinline__ void ratio_table(T X, T (&xk)[W]) {
 #pragma unroll
-    for (int k = 0; k < W; ++k) xk[k] = X * (T(1) / T(k + 1));
+    for (int k = 0; k < W; ++k) xk[k] = X * Num<T>::recip(k + 1);
 }
 
 // P <- P * Ebar(x) on the window, in Horner form: with xk[k] = x/(k+1),
@@ -316,59 +381,63 @@ __device__ __forceinline__ void emit_fast(const EdgeOutArgs &o, int t, T val, T 
 // accesses to one k hit 32 consecutive words.
 constexpr int kLS = 32;
 
-// All contributions of one edge.  Xs[i*kLS]: the member values; Pre: this
-// lane's column for Pre_2..Pre_{s-1}; ib/sb: its member ids / incidence slots.
+// All contributions of one edge.  Xs[i*kLS]: the member values (type In); Pre:
+// this lane's column for Pre_2..Pre_{s-1}; ib/sb: its member ids / incidence slots.
 template <typename T, int W, bool BUF>
-__device__ __forceinline__ void edge_compute(const EdgeBucketArgs &b, const EdgeOutArgs &o, const T *Xs, T *Pre,
-                                             const int32_t *ib, const int32_t *sb, int s) {
-    T S = T(0);
-    for (int i = 0; i < s; ++i) S += Arith<T>::absv(Xs[i * kLS]);
-    const int p = scale_exponent<T>(S, b.target);
-    const T g = Arith<T>::pow2(p);
+__device__ __forceinline__ void edge_compute(const EdgeBucketArgs &b, const EdgeOutArgs &o,
+                                             const typename Num<T>::In *Xs, T *Pre, const int32_t *ib,
+                                             const int32_t *sb, int s) {
+    using In = typename Num<T>::In;
+    using Out = typename Num<T>::Out;
+    In S = In(0);
+    for (int i = 0; i < s; ++i) S += Arith<In>::absv(Xs[i * kLS]);
+    const int p = scale_exponent<In>(S, b.target);
+    const In g = Arith<In>::pow2(p);
     const int32_t *ob = BUF ? sb : ib;  // where each member's result goes
-    const EdgeScale<T> sc = edge_scale(b, o, p, T(0));
+    const EdgeScale<Out> sc = edge_scale(b, o, p, Out(0));
     int nbad = 0;
-    auto emit = [&](int q, T val, T xhat) {
+    auto emit = [&](int q, T val, In xhat) {
         const int t = ob[q * kLS];
-        if (sc.fast) emit_fast<T, BUF>(o, t, val, sc.mult, nbad);
-        else emit_value<T, BUF>(b, o, t, t, val, p, xhat);
+        const Out v = Num<T>::out(val);
+        if (sc.fast) emit_fast<Out, BUF>(o, t, v, sc.mult, nbad);
+        else emit_value<Out, BUF>(b, o, t, t, v, p, xhat);
     };
 
     // forward: P = Pre_2, then Pre_3 .. Pre_s (windows Pre_2..Pre_{s-1} kept in shared memory)
     T P[W];
-    power_table<T, W>(Xs[0] * g, P);
+    power_table<T, W>(Num<T>::cvt(Xs[0] * g), P);
     for (int i = 1; i <= s - 2; ++i) {
         T *slot = Pre + (i - 1) * W * kLS;
 #pragma unroll
         for (int j = 0; j < W; ++j) slot[j * kLS] = P[j];
         T xk[W];
-        ratio_table<T, W>(Xs[i * kLS] * g, xk);
+        ratio_table<T, W>(Num<T>::cvt(Xs[i * kLS] * g), xk);
         toeplitz_horner<T, W>(P, xk);
     }
     // P = Pre_s.  backward: Q = Suf_{s-1} = Ebar(x_{v_s})
     T Q[W];
-    const T xs_last = Xs[(s - 1) * kLS] * g;
-    power_table<T, W>(xs_last, Q);
-    T F = T(0);
+    const In xs_last = Xs[(s - 1) * kLS] * g;
+    power_table<T, W>(Num<T>::cvt(xs_last), Q);
+    T F = Num<T>::zero();
 #pragma unroll
     for (int j = 0; j <= W - 2; ++j) F = Arith<T>::fma_(P[j], Q[W - 2 - j], F);
-    emit(s - 1, F + P[W - 1], xs_last);
-    T top = T(0);
+    emit(s - 1, Num<T>::add(F, P[W - 1]), xs_last);
+    T top = Num<T>::zero();
     for (int q = s - 2; q >= 1; --q) {
         // Q = Suf_{q+1}; Pre_{q+1} sits in slot q-1
         const T *slot = Pre + (q - 1) * W * kLS;
-        T D = T(0);
+        T D = Num<T>::zero();
 #pragma unroll
         for (int j = 0; j < W; ++j) D = Arith<T>::fma_(slot[j * kLS], Q[W - 1 - j], D);
-        const T xq = Xs[q * kLS] * g;
-        emit(q, F + D, xq);
+        const In xq = Xs[q * kLS] * g;
+        emit(q, Num<T>::add(F, D), xq);
         T xk[W];
-        ratio_table<T, W>(xq, xk);
+        ratio_table<T, W>(Num<T>::cvt(xq), xk);
         if (q >= 2) toeplitz_horner<T, W>(Q, xk);
         else top = top_horner<T, W>(Q, xk);
     }
     T D1 = (s == 2) ? Q[W - 1] : top;
-    emit(0, F + D1, Xs[0] * g);
+    emit(0, Num<T>::add(F, D1), Xs[0] * g);
     if (nbad && o.range_events) atomicAdd(o.range_events, (unsigned long long)nbad);
 }
 
@@ -384,8 +453,10 @@ __host__ __device__ constexpr size_t thread_smem_words(int s, int W) {
 // and the id/slot loads of edge k+2 are in flight.  Ring buffers rotate by
 // pointer; global addresses advance by the grid stride.
 template <typename T, int W, bool BUF>
-__global__ void __launch_bounds__(256) edge_thread_kernel(EdgeBucketArgs b, const T *__restrict__ x,
+__global__ void __launch_bounds__(256) edge_thread_kernel(EdgeBucketArgs b, const typename Num<T>::In *__restrict__ x,
                                                           EdgeOutArgs o) {
+    using In = typename Num<T>::In;
+    static_assert(sizeof(In) == sizeof(T), "member values and series values share the element size");
     if (o.skip && *o.skip) return;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int BS = blockDim.x;
@@ -393,9 +464,9 @@ __global__ void __launch_bounds__(256) edge_thread_kernel(EdgeBucketArgs b, cons
     const int s = b.s;
     const size_t words = thread_smem_words<T>(s, W);
     T *wb = reinterpret_cast<T *>(smem_raw + (size_t)(tid >> 5) * words * 4 * kLS);  // this warp's region
-    T *xc = wb + lane;                   // X of the edge being computed
-    T *xn = xc + s * kLS;                // X of the next edge (in flight)
-    T *Pre = xc + 2 * s * kLS;
+    In *xc = reinterpret_cast<In *>(wb) + lane;   // X of the edge being computed
+    In *xn = xc + s * kLS;                        // X of the next edge (in flight)
+    T *Pre = wb + 2 * s * kLS + lane;
     int32_t *ibase = reinterpret_cast<int32_t *>(wb + (2 * s + (s > 2 ? (s - 2) * W : 0)) * kLS) + lane;
     const int ring = s * kLS;
     // ring slots (ids; the slots array sits 3 rings further): current, next, after next
@@ -417,8 +488,8 @@ __global__ void __launch_bounds__(256) edge_thread_kernel(EdgeBucketArgs b, cons
             gs += ld;
         }
     };
-    auto issue_x = [&](const int32_t *src, T *xb) {
-        for (int i = 0; i < s; ++i) cp_async<(int)sizeof(T)>(xb + i * kLS, x + src[i * kLS]);
+    auto issue_x = [&](const int32_t *src, In *xb) {
+        for (int i = 0; i < s; ++i) cp_async<(int)sizeof(In)>(xb + i * kLS, x + src[i * kLS]);
     };
 
     issue_ids(gid, gsl, r0);
@@ -439,7 +510,7 @@ __global__ void __launch_bounds__(256) edge_thread_kernel(EdgeBucketArgs b, cons
         r0 = r1;
         r1 = r2;
         r2 = t;
-        T *tx = xc;
+        In *tx = xc;
         xc = xn;
         xn = tx;
     }
@@ -457,7 +528,10 @@ __global__ void __launch_bounds__(256) edge_thread_kernel(EdgeBucketArgs b, cons
 constexpr int kPairEdges = 4;
 
 template <typename T, int W, bool BUF>
-__global__ void __launch_bounds__(256, 4) edge_pair_kernel(EdgeBucketArgs b, const T *__restrict__ x, EdgeOutArgs o) {
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 2) edge_pair_kernel(EdgeBucketArgs b, const typename Num<T>::In *__restrict__ x,
+                                                           EdgeOutArgs o) {
+    using In = typename Num<T>::In;
+    using Out = typename Num<T>::Out;
     if (o.skip && *o.skip) return;
     constexpr int E = kPairEdges;
     const int64_t span = (int64_t)blockDim.x * E;
@@ -465,7 +539,7 @@ __global__ void __launch_bounds__(256, 4) edge_pair_kernel(EdgeBucketArgs b, con
     int nbad = 0;
     for (int64_t e0 = (int64_t)blockIdx.x * span + threadIdx.x; e0 < b.m; e0 += stride) {
         int v0[E], v1[E], t0[E], t1[E];
-        T X0[E], X1[E];
+        In X0[E], X1[E];
 #pragma unroll
         for (int k = 0; k < E; ++k) {
             const int64_t e = e0 + (int64_t)k * blockDim.x;
@@ -483,24 +557,26 @@ __global__ void __launch_bounds__(256, 4) edge_pair_kernel(EdgeBucketArgs b, con
 #pragma unroll
         for (int k = 0; k < E; ++k) {
             if (e0 + (int64_t)k * blockDim.x >= b.m) break;
-            const int p = scale_exponent<T>(Arith<T>::absv(X0[k]) + Arith<T>::absv(X1[k]), b.target);
-            const T g = Arith<T>::pow2(p);
-            const T a0 = X0[k] * g, a1 = X1[k] * g;
+            const int p = scale_exponent<In>(Arith<In>::absv(X0[k]) + Arith<In>::absv(X1[k]), b.target);
+            const In g = Arith<In>::pow2(p);
+            const In a0x = X0[k] * g, a1x = X1[k] * g;
+            const T a0 = Num<T>::cvt(a0x), a1 = Num<T>::cvt(a1x);
             T Q[W];
             power_table<T, W>(a1, Q);
-            T P = a0, F = T(0);
+            T P = a0, F = Num<T>::zero();
 #pragma unroll
             for (int j = 0; j <= W - 2; ++j) {
                 F = Arith<T>::fma_(P, Q[W - 2 - j], F);
-                P = P * (a0 * (T(1) / T(j + 2)));
+                P = P * (a0 * Num<T>::recip(j + 2));
             }
-            const EdgeScale<T> sc = edge_scale(b, o, p, T(0));
+            const Out c1 = Num<T>::out(Num<T>::add(F, P)), c0 = Num<T>::out(Num<T>::add(F, Q[W - 1]));
+            const EdgeScale<Out> sc = edge_scale(b, o, p, Out(0));
             if (sc.fast) {
-                emit_fast<T, BUF>(o, t1[k], F + P, sc.mult, nbad);
-                emit_fast<T, BUF>(o, t0[k], F + Q[W - 1], sc.mult, nbad);
+                emit_fast<Out, BUF>(o, t1[k], c1, sc.mult, nbad);
+                emit_fast<Out, BUF>(o, t0[k], c0, sc.mult, nbad);
             } else {
-                emit_value<T, BUF>(b, o, t1[k], t1[k], F + P, p, a1);
-                emit_value<T, BUF>(b, o, t0[k], t0[k], F + Q[W - 1], p, a0);
+                emit_value<Out, BUF>(b, o, t1[k], t1[k], c1, p, a1x);
+                emit_value<Out, BUF>(b, o, t0[k], t0[k], c0, p, a0x);
             }
         }
     }
@@ -514,12 +590,13 @@ __global__ void __launch_bounds__(256, 4) edge_pair_kernel(EdgeBucketArgs b, con
 // s3_kernels.h counts its 4-byte words.  Every warp's region holds lane_words
 // words per lane (the largest need of the launch's buckets).
 template <typename T, int W, bool BUF>
-__device__ __forceinline__ void tail_edge(const EdgeBucketArgs &b, const T *__restrict__ x, const EdgeOutArgs &o,
-                                          int64_t e, unsigned char *smem_raw, int lane_words) {
+__device__ __forceinline__ void tail_edge(const EdgeBucketArgs &b, const typename Num<T>::In *__restrict__ x,
+                                          const EdgeOutArgs &o, int64_t e, unsigned char *smem_raw, int lane_words) {
+    using In = typename Num<T>::In;
     const int tid = threadIdx.x, lane = tid & 31, s = b.s;
     T *wb = reinterpret_cast<T *>(smem_raw + (size_t)(tid >> 5) * lane_words * 4 * kLS);
-    T *xs = wb + lane;
-    T *Pre = xs + s * kLS;
+    In *xs = reinterpret_cast<In *>(wb) + lane;
+    T *Pre = wb + s * kLS + lane;
     int32_t *ib = reinterpret_cast<int32_t *>(wb + (s + (s > 2 ? (s - 2) * W : 0)) * kLS) + lane;
     int32_t *sb = ib + s * kLS;
     for (int i = 0; i < s; ++i) {
@@ -528,7 +605,7 @@ __device__ __forceinline__ void tail_edge(const EdgeBucketArgs &b, const T *__re
     }
     cp_async_commit();
     cp_async_wait_all();
-    for (int i = 0; i < s; ++i) cp_async<(int)sizeof(T)>(xs + i * kLS, x + ib[i * kLS]);
+    for (int i = 0; i < s; ++i) cp_async<(int)sizeof(In)>(xs + i * kLS, x + ib[i * kLS]);
     cp_async_commit();
     cp_async_wait_all();
     edge_compute<T, W, BUF>(b, o, xs, Pre, ib, sb, s);
@@ -540,7 +617,7 @@ __device__ __forceinline__ void tail_edge(const EdgeBucketArgs &b, const T *__re
 // so one launch for all of them pays that latency once instead of per bucket.
 template <typename T, bool BUF>
 __global__ void __launch_bounds__(128) edge_tail_kernel(const TailEntry *__restrict__ tab, int ntab, int lane_words,
-                                                        const T *__restrict__ x, EdgeOutArgs o) {
+                                                        const typename Num<T>::In *__restrict__ x, EdgeOutArgs o) {
     if (o.skip && *o.skip) return;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     int k = 0;
@@ -740,7 +817,8 @@ constexpr size_t kSmemCapWarp = 200 * 1024;   // per block, warp-per-edge kernel
 constexpr int kMaxThreadW = 32;
 
 template <typename T, int W, bool BUF>
-cudaError_t launch_thread_wb(const EdgeBucketArgs &b, const T *x, const EdgeOutArgs &o, int bs, cudaStream_t st) {
+cudaError_t launch_thread_wb(const EdgeBucketArgs &b, const typename Num<T>::In *x, const EdgeOutArgs &o, int bs,
+                             cudaStream_t st) {
     size_t smem = thread_smem_words<T>(b.s, W) * 4 * (size_t)bs;
     // enough blocks to fill the GPU (several edges per thread beyond that)
     static int sms = 0;
@@ -764,7 +842,8 @@ cudaError_t launch_thread_wb(const EdgeBucketArgs &b, const T *x, const EdgeOutA
 }
 
 template <typename T, int W>
-cudaError_t launch_thread_w(const EdgeBucketArgs &b, const T *x, const EdgeOutArgs &o, int bs, cudaStream_t st) {
+cudaError_t launch_thread_w(const EdgeBucketArgs &b, const typename Num<T>::In *x, const EdgeOutArgs &o, int bs,
+                            cudaStream_t st) {
     return o.mode == kOutBuffer ? launch_thread_wb<T, W, true>(b, x, o, bs, st)
                                 : launch_thread_wb<T, W, false>(b, x, o, bs, st);
 }
@@ -814,7 +893,8 @@ int64_t full_grid() {
 }
 
 template <typename T, int W>
-cudaError_t launch_pair_w(const EdgeBucketArgs &b, const T *x, const EdgeOutArgs &o, cudaStream_t st) {
+cudaError_t launch_pair_w(const EdgeBucketArgs &b, const typename Num<T>::In *x, const EdgeOutArgs &o,
+                          cudaStream_t st) {
     constexpr int bs = 256;
     const int64_t need = (b.m + bs - 1) / bs;
     if (o.mode == kOutBuffer) {
@@ -830,8 +910,8 @@ cudaError_t launch_pair_w(const EdgeBucketArgs &b, const T *x, const EdgeOutArgs
 // The fused launch of the small buckets listed in tab (device memory, ntab entries,
 // nblocks blocks of bs threads in total, smem bytes of dynamic shared memory).
 template <typename T>
-cudaError_t launch_edge_tail_t(const TailEntry *tab, int ntab, int64_t nblocks, int bs, size_t smem, const T *x,
-                               const EdgeOutArgs &o, cudaStream_t st) {
+cudaError_t launch_edge_tail_t(const TailEntry *tab, int ntab, int64_t nblocks, int bs, size_t smem,
+                               const typename Num<T>::In *x, const EdgeOutArgs &o, cudaStream_t st) {
     if (ntab <= 0 || nblocks <= 0) return cudaSuccess;
     if (smem > kSmemCap || nblocks > INT32_MAX) return cudaErrorInvalidConfiguration;
     const int lane_words = (int)(smem / 4 / (size_t)bs);
@@ -853,13 +933,15 @@ int thread_block_size(int s, int W, int want) {
 }
 
 template <typename T>
-cudaError_t launch_edge_bucket_t(const EdgeBucketArgs &b, const T *x, const EdgeOutArgs &o, int thread_max_w,
-                                 int block_threads, cudaStream_t st) {
+cudaError_t launch_edge_bucket_t(const EdgeBucketArgs &b, const typename Num<T>::In *x, const EdgeOutArgs &o,
+                                 int thread_max_w, int block_threads, cudaStream_t st) {
     if (b.m <= 0) return cudaSuccess;
-    if (b.s == 1) {
-        int bs = 256;
-        edge_single_kernel<T><<<(unsigned)((b.m + bs - 1) / bs), bs, 0, st>>>(b, x, o);
-        return cudaGetLastError();
+    {
+        if (b.s == 1) {
+            int bs = 256;
+            edge_single_kernel<T><<<(unsigned)((b.m + bs - 1) / bs), bs, 0, st>>>(b, x, o);
+            return cudaGetLastError();
+        }
     }
     const int W = b.N - b.s + 1;
     if (thread_max_w <= 0 || thread_max_w > kMaxThreadW) thread_max_w = kMaxThreadW;
@@ -885,22 +967,24 @@ cudaError_t launch_edge_bucket_t(const EdgeBucketArgs &b, const T *x, const Edge
             }
         }
     }
-    // wide windows: four lanes per edge (s3_group.cuh) when eight edges fit a warp's shared memory
     {
-        int launched = 0;
-        cudaError_t e = launch_edge_group(b, x, o, W, st, &launched);
-        if (e != cudaSuccess || launched) return e;
+        // wide windows: eight lanes per edge (s3_group.cuh) when four edges fit a warp's shared memory
+        {
+            int launched = 0;
+            cudaError_t e = launch_edge_group(b, x, o, W, st, &launched);
+            if (e != cudaSuccess || launched) return e;
+        }
+        // one warp per edge
+        int64_t per_warp = warp_smem_elems(b.s, W);
+        int wpb = 4;
+        while (wpb > 1 && (size_t)wpb * per_warp * sizeof(T) > kSmemCapWarp) wpb /= 2;
+        size_t smem = (size_t)wpb * per_warp * sizeof(T);
+        if (smem > kSmemCapWarp) return cudaErrorInvalidConfiguration;
+        int64_t grid = (b.m + wpb - 1) / wpb;
+        if (grid > (1 << 22)) grid = 1 << 22;
+        edge_warp_kernel<T><<<(unsigned)grid, wpb * 32, smem, st>>>(b, x, o, W, per_warp);
+        return cudaGetLastError();
     }
-    // one warp per edge
-    int64_t per_warp = warp_smem_elems(b.s, W);
-    int wpb = 4;
-    while (wpb > 1 && (size_t)wpb * per_warp * sizeof(T) > kSmemCapWarp) wpb /= 2;
-    size_t smem = (size_t)wpb * per_warp * sizeof(T);
-    if (smem > kSmemCapWarp) return cudaErrorInvalidConfiguration;
-    int64_t grid = (b.m + wpb - 1) / wpb;
-    if (grid > (1 << 22)) grid = 1 << 22;
-    edge_warp_kernel<T><<<(unsigned)grid, wpb * 32, smem, st>>>(b, x, o, W, per_warp);
-    return cudaGetLastError();
 }
 
 }  // namespace s3

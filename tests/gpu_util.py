@@ -21,13 +21,14 @@ def gpu_sttsvc(hg, x, dtype="f64", layout=None, rank=None, **opts):
     if layout == "ccss":
         kw["build_ccss"] = 1
     g = s3.s3_build_format(hg.n, hg.edge_ptr, hg.members, **kw)
-    dt = torch.float64 if dtype == "f64" else torch.float32
+    dt = torch.float32 if dtype == "f32" else torch.float64
+    df = dtype == "df"   # FP64 vectors, double-float series
     xd = torch.tensor(np.asarray(x), dtype=dt, device="cuda")
     yd = torch.full_like(xd, float("nan"))
     if layout == "ccss":
-        s3.s3_sttsvc_layout(g, s3.S3_LAYOUT_CCSS, xd, yd)
+        s3.s3_sttsvc_layout(g, s3.S3_LAYOUT_CCSS, xd, yd, df=df)
     else:
-        s3.s3_sttsvc(g, xd, yd)
+        s3.s3_sttsvc(g, xd, yd, df=df)
     torch.cuda.synchronize()
     out = yd.double().cpu().numpy()
     s3.s3_destroy(g)

@@ -42,6 +42,18 @@ def test_fp32_mixed_reaches_same_vector(medium):
     print(f"mixed: {res['iters']} iterations ({res['iters_fp32']} FP32), oracle {ref.iters}")
 
 
+@pytest.mark.parametrize("precision", [2, 3])
+def test_double_float_phases_reach_same_vector(medium, precision):
+    # 2: FP32 then double-float series; 3: double-float series throughout
+    hg, ref = medium
+    x, res = _run(hg, tol=1e-8, precision=precision)
+    assert res["converged"]
+    assert (res["iters_fp32"] > 0) == (precision == 2)
+    assert np.max(np.abs(x - ref.x) / ref.x) < 1e-7
+    if precision == 3:
+        assert abs(res["iters"] - ref.iters) <= 1
+
+
 def test_regular_hypergraph_one_iteration():
     hg = regular_hypergraph(300, 4, 2, 7, 2)
     x, res = _run(hg, tol=1e-12)

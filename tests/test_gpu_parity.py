@@ -17,12 +17,12 @@ F64_TOL = 1e-12
 F32_TOL = 1e-5
 
 
-def check(hg, x, N=None, layouts=(None,), reduces=(0, 1), f32_tol=F32_TOL, f64_tol=F64_TOL, **opts):
+def check(hg, x, N=None, layouts=(None,), reduces=(0, 1), f32_tol=F32_TOL, f64_tol=F64_TOL, dtypes=None, **opts):
     want = oracle.ttsv1(hg, x, N=N)
     errs = {}
     for layout in layouts:
         for red in reduces:
-            for dt, tol in (("f64", f64_tol), ("f32", f32_tol)):
+            for dt, tol in (dtypes or (("f64", f64_tol), ("f32", f32_tol))):
                 y = gpu_sttsvc(hg, x, dt, layout=layout, rank=N, reduce=red, **opts)
                 e = rel_err(y, want)
                 errs[(layout, red, dt)] = e
@@ -80,6 +80,37 @@ def test_size_two_edges_all_ranks():
     x = s3synth.x_uniform(hg.n, 0.1, 1.4, 4)
     for N in (2, 3, 9, 25, 33, 34, 40):
         check(hg, x, N=N, reduces=(0, 1), small_bucket_edges=-1)
+
+
+DF_TOL = 1e-11   # double-float series: ~44-bit significands, ~1e-13 per node in practice
+
+
+def test_double_float_series():
+    # S3_DF64: FP64 x and y, series in pairs of FP32 numbers; windows wider than 24 and
+    # size-1 edges fall back to FP64 kernels, CCSS runs FP64
+    for hg, x, N in ((s3synth.config_small(seed=4), None, None),
+                     (s3synth.config_powerlaw(n=20000, m=100000, rank=25, seed=14), None, None),
+                     (s3synth.tiny_case(seed=3, rank=4), None, 6),
+                     (s3synth.config_large_rank(n=3000, m=4000, rank=100, seed=15), None, None)):
+        x = s3synth.x_uniform(hg.n, 0.05, 1.5, 21)
+        errs = check(hg, x, N=N, dtypes=(("df", DF_TOL),), layouts=(None, "ccss"))
+        print(hg.name, {k: f"{v:.1e}" for k, v in errs.items()})
+    # every window 1..32 through the size-2 and thread kernels, blocks of 64 threads
+    rng = np.random.default_rng(8)
+    edges = [tuple(rng.choice(300, size=s, replace=False)) for s in (2, 3, 5, 9) for _ in range(400)]
+    hg = s3synth.from_edges(300, edges)
+    x = s3synth.x_uniform(hg.n, 0.2, 1.1, 22)
+    for N in (9, 17, 25, 33):
+        check(hg, x, N=N, dtypes=(("df", DF_TOL),), block_threads=64, small_bucket_edges=-1)
+
+
+def test_double_float_matches_fp64_closely():
+    hg = s3synth.config_powerlaw(n=20000, m=100000, rank=25, seed=16)
+    x = s3synth.x_uniform(hg.n, 0.3, 1.2, 23)
+    a = gpu_sttsvc(hg, x, "df")
+    b = gpu_sttsvc(hg, x, "f64")
+    m = b != 0
+    assert np.max(np.abs(a[m] - b[m]) / np.abs(b[m])) < 1e-12
 
 
 def test_large_rank_100():
