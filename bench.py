@@ -319,6 +319,19 @@ def run_gpu(args):
     ms64 = (time.perf_counter() - st64) * 1e3 / reps64
     out["fp64"] = {"value": nnz / (ms64 * 1e-3), "unit": UNIT, "ms_per_call": ms64,
                    "fp32_speedup": ms64 / ms}
+    # FP64 in and out with the series in double-float (pairs of FP32)
+    ydf = torch.empty_like(y64)
+    s3.s3_sttsvc(g, x64, ydf, df=True)
+    torch.cuda.synchronize()
+    stdf = time.perf_counter()
+    for _ in range(reps64):
+        s3.s3_sttsvc(g, x64, ydf, df=True)
+    torch.cuda.synchronize()
+    msdf = (time.perf_counter() - stdf) * 1e3 / reps64
+    a, b = ydf.cpu().numpy(), y64.cpu().numpy()
+    nz = b != 0
+    out["df64"] = {"value": nnz / (msdf * 1e-3), "unit": UNIT, "ms_per_call": msdf, "speedup_vs_fp64": ms64 / msdf,
+                   "max_rel_diff_vs_fp64": float(np.max(np.abs(a[nz] - b[nz]) / np.abs(b[nz])))}
     # end to end through the host-buffer entry point
     xh = x.cpu().pin_memory()
     yh = torch.empty_like(xh).pin_memory()
@@ -416,7 +429,7 @@ def warm_start(lcc, dev, graphs=48, n=50000, epochs=20):
     model, hist = ws.train(feat, tgt, epochs=epochs, batch=65536, lr=2e-3)
     t_train = time.perf_counter() - t0
     out = {}
-    for name, prec in (("fp64", 0), ("fp32_mixed", 1)):
+    for name, prec in (("fp64", 0), ("fp32_mixed", 1), ("fp32_then_double_float", 2), ("double_float", 3)):
         out[name] = ws.evaluate(lcc, model, tol=1e-8, precision=prec)
     out.update({"train_graphs": graphs, "train_n": n, "train_nodes": int(feat.shape[0]), "epochs": epochs,
                 "loss_first": hist[0][1], "loss_last": hist[-1][1], "data_s": t_data, "train_s": t_train})
@@ -508,7 +521,8 @@ def layouts(dev):
 
 
 def centrality(hg, dev):
-    """NQZ to 1e-8 on the largest connected component: FP32-mixed vs plain FP64."""
+    """NQZ to 1e-8 on the largest connected component: plain FP64 vs FP32 series with an FP64 or a
+    double-float finish, and double-float throughout (each after one untimed run)."""
     import torch
 
     import paper_2311_08595_gb300 as s3
@@ -517,7 +531,8 @@ def centrality(hg, dev):
     g = s3.s3_build_format(lcc.n, lcc.edge_ptr, lcc.members)
     res = {}
     xs = {}
-    for name, prec in (("fp64", 0), ("fp32_mixed", 1)):
+    for name, prec in (("fp64", 0), ("fp32_mixed", 1), ("fp32_then_double_float", 2), ("double_float", 3)):
+        s3.s3_hcentrality(g, tol=1e-8, precision=prec, raise_on_noconv=False)   # untimed: scratch, graphs
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         xo, r = s3.s3_hcentrality(g, tol=1e-8, precision=prec, raise_on_noconv=False)
@@ -529,6 +544,9 @@ def centrality(hg, dev):
     res["n_lcc"] = lcc.n
     res["speedup_fp32_mixed"] = res["fp64"]["wall_s"] / res["fp32_mixed"]["wall_s"]
     res["max_rel_diff_x"] = float(np.max(np.abs(xs["fp32_mixed"] - xs["fp64"]) / xs["fp64"]))
+    for name in ("fp32_then_double_float", "double_float"):
+        res[name]["speedup_vs_fp64"] = res["fp64"]["wall_s"] / res[name]["wall_s"]
+        res[name]["max_rel_diff_x"] = float(np.max(np.abs(xs[name] - xs["fp64"]) / xs["fp64"]))
     s3.s3_destroy(g)
     if WARM_GRAPHS > 0:
         res["learned_warm_start"] = warm_start(lcc, dev, graphs=WARM_GRAPHS)
