@@ -216,7 +216,9 @@ typedef struct {
                               3 = double-float series throughout.  Norms, roots, ratios and
                               the bracket are FP64 in every mode. */
     double switch_tol;     /* FP32 -> FP64 hand-over gap for precision 1 and 2; <= 0 = 1e-5 */
-    int32_t check_every;   /* iterations per captured CUDA graph between host checks; <= 0 = 8 */
+    int32_t check_every;   /* iterations per captured CUDA graph between host checks; <= 0 = 8.
+                              The graphs are kept on the handle for later calls with the same
+                              tol, max_iter and check_every (freed by s3_destroy). */
     int32_t reserved[7];
 } s3_nqz_options;
 

@@ -53,6 +53,11 @@ s3_status upload(s3_graph_s *g, T **dst, const std::vector<T> &src) {
 }
 
 void free_all(s3_graph_s *g) {
+    for (auto &x : g->nqz_exec)
+        if (x.exec) {
+            cudaGraphExecDestroy(x.exec);
+            x.exec = nullptr;
+        }
     for (void *p : g->allocations) cudaFree(p);
     g->allocations.clear();
     for (int i = 0; i < 8; ++i) {
@@ -277,6 +282,11 @@ s3_status s3_build_format(int64_t n, int64_t m, const int64_t *edge_ptr, const i
         return bail(cuda_fail(cudaGetLastError(), "memset"));
     if ((st = upload(g, &g->d_piece_start, f.piece_start)) != S3_OK) return bail(st);
     if ((st = upload(g, &g->d_piece_len, f.piece_len)) != S3_OK) return bail(st);
+    for (int64_t v = 0; v < f.n; ++v)
+        if (f.inc_ptr[v + 1] == f.inc_ptr[v]) {
+            g->first_isolated = v;
+            break;
+        }
     g->n_grp = (int64_t)f.grp_off.size();
     g->n_med8 = (int64_t)f.med8_node.size();
     g->n_med = (int64_t)f.med_node.size();

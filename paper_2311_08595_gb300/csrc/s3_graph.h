@@ -69,6 +69,14 @@ struct s3_graph_s {
     int32_t *d_flags = nullptr;     // [0] done, [1] phase-switch, ...
     double *d_hist = nullptr;       // per-iteration (lmin, lmax)
     int32_t hist_cap = 0;
+    int64_t first_isolated = -1;    // a node of degree 0 (NQZ rejects the handle), or -1
+    // captured NQZ passes, kept for later calls with the same settings: one per series type
+    struct NqzExec {
+        cudaGraphExec_t exec = nullptr;
+        double tol = 0.0;
+        int32_t max_iter = 0, check_every = 0;
+        const double *hist = nullptr;
+    } nqz_exec[3];
 
     int32_t last_launches = 0;       // kernels launched by the last S^3TTVc call
     uint32_t *d_feat_scratch = nullptr;  // warm-start feature counters (48 bytes per node)

@@ -14,7 +14,9 @@
 // shrinking or drops below switch_tol and then FP64 or double-float (pairs of
 // FP32, S3_DF64), or double-float throughout (the precision option).
 // Iterations run in captured CUDA graphs of `check_every` steps; a device flag
-// turns the remaining launches of a graph into no-ops once the test passes.
+// turns the remaining launches of a graph into no-ops once the test passes.  The
+// instantiated graphs stay on the handle and are replayed by later calls with
+// the same tolerance, iteration cap and graph length.
 #include <cuda_runtime.h>
 
 #include <chrono>
@@ -285,21 +287,10 @@ s3_status s3_hcentrality(s3_graph_t g, const s3_nqz_options *opt_in, const doubl
         S3_CUDA(cudaStreamCreate(&own.s));
         st = own.s;
     }
-    struct Execs {
-        cudaGraphExec_t e[2] = {nullptr, nullptr};
-        ~Execs() {
-            for (auto x : e)
-                if (x) cudaGraphExecDestroy(x);
-        }
-    } execs;
     std::memset(res, 0, sizeof(*res));
-    // reject isolated nodes
-    {
-        std::vector<int64_t> ptr(g->n + 1);
-        S3_CUDA(cudaMemcpy(ptr.data(), g->d_inc_ptr, sizeof(int64_t) * (g->n + 1), cudaMemcpyDeviceToHost));
-        for (int64_t v = 0; v < g->n; ++v)
-            if (ptr[v + 1] == ptr[v]) return fail(S3_EINVAL, "node " + std::to_string(v) + " belongs to no edge");
-    }
+    // isolated nodes (found when the handle was built) make the ratio 0/0
+    if (g->first_isolated >= 0)
+        return fail(S3_EINVAL, "node " + std::to_string(g->first_isolated) + " belongs to no edge");
     s3_status s = ensure_nqz_scratch(g, opt.max_iter + 2);
     if (s != S3_OK) return s;
     NqzBufs b;
@@ -350,7 +341,14 @@ s3_status s3_hcentrality(s3_graph_t g, const s3_nqz_options *opt_in, const doubl
             if (s != S3_OK) return s;
             last_z = phase;
         } else {
-            cudaGraphExec_t &exec = execs.e[phase == S3_F32 ? 0 : 1];
+            // captured passes are kept on the handle and reused while the settings match
+            s3_graph_s::NqzExec &ce_ = g->nqz_exec[phase == S3_F32 ? 0 : phase == S3_F64 ? 1 : 2];
+            if (ce_.exec && (ce_.tol != tol || ce_.max_iter != opt.max_iter || ce_.check_every != opt.check_every ||
+                             ce_.hist != g->d_hist)) {
+                cudaGraphExecDestroy(ce_.exec);
+                ce_.exec = nullptr;
+            }
+            cudaGraphExec_t &exec = ce_.exec;
             if (!exec) {
                 cudaGraph_t graph = nullptr;
                 S3_CUDA(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
@@ -366,6 +364,10 @@ s3_status s3_hcentrality(s3_graph_t g, const s3_nqz_options *opt_in, const doubl
                 ce = cudaGraphInstantiate(&exec, graph, 0);
                 cudaGraphDestroy(graph);
                 S3_CUDA(ce);
+                ce_.tol = tol;
+                ce_.max_iter = opt.max_iter;
+                ce_.check_every = opt.check_every;
+                ce_.hist = g->d_hist;
             }
             S3_CUDA(cudaGraphLaunch(exec, st));
         }

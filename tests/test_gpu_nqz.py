@@ -54,6 +54,21 @@ def test_double_float_phases_reach_same_vector(medium, precision):
         assert abs(res["iters"] - ref.iters) <= 1
 
 
+def test_repeated_calls_reuse_graphs(medium):
+    # the captured passes stay on the handle: same settings -> same result; other settings recapture
+    import paper_2311_08595_gb300 as s3
+    hg, ref = medium
+    g = s3.s3_build_format(hg.n, hg.edge_ptr, hg.members)
+    x1, r1 = s3.s3_hcentrality(g, tol=1e-8, precision=2)
+    x2, r2 = s3.s3_hcentrality(g, tol=1e-8, precision=2)
+    assert r1["iters"] == r2["iters"] and bool((x1 == x2).all())
+    x3, r3 = s3.s3_hcentrality(g, tol=1e-6, precision=2, check_every=4)
+    assert r3["converged"] and r3["iters"] < r1["iters"]
+    x4, r4 = s3.s3_hcentrality(g, tol=1e-8, precision=2)
+    assert r4["iters"] == r1["iters"] and bool((x4 == x1).all())
+    assert np.max(np.abs(x4.cpu().numpy() - ref.x) / ref.x) < 1e-7
+
+
 def test_regular_hypergraph_one_iteration():
     hg = regular_hypergraph(300, 4, 2, 7, 2)
     x, res = _run(hg, tol=1e-12)
