@@ -113,7 +113,18 @@ __device__ __forceinline__ DF df_from(double d) {
 __device__ __forceinline__ double df_to(DF a) { return (double)a.hi + (double)a.lo; }
 
 template <> struct Arith<DF> {
-    __device__ __forceinline__ static DF fma_(DF a, DF b, DF c) { return a * b + c; }
+    // a b + c with one exact product error and one error-free sum; the result is left
+    // unnormalised (its low part stays within a few units of the high part's last
+    // place), which is all the accumulation chains of the window products need
+    __device__ __forceinline__ static DF fma_(DF a, DF b, DF c) {
+        const float p = __fmul_rn(a.hi, b.hi);
+        const float ep = __fmaf_rn(a.hi, b.hi, -p);
+        const float s = __fadd_rn(p, c.hi);
+        const float bb = __fsub_rn(s, p);
+        const float es = __fadd_rn(__fsub_rn(p, __fsub_rn(s, bb)), __fsub_rn(c.hi, bb));
+        const float lo = __fmaf_rn(a.hi, b.lo, __fmaf_rn(a.lo, b.hi, __fadd_rn(__fadd_rn(ep, c.lo), es)));
+        return DF{s, lo};
+    }
 };
 
 // Value types of a kernel instance: T is the arithmetic of the series, In the
