@@ -69,8 +69,10 @@ typedef enum {
 typedef enum { S3_F32 = 0, S3_F64 = 1, S3_DF64 = 2 } s3_dtype;
 
 typedef enum {
-    /* y_v is summed node by node from a per-(edge, node) buffer laid out in
-     * node-sorted incidence order: deterministic, bit-identical run to run. */
+    /* y_v is summed node by node from a per-(edge, node) buffer laid out by
+     * node (groups of 32 low-degree nodes interleaved, one segment per other
+     * node, hubs in fixed pieces), each sum in a fixed order: deterministic,
+     * bit-identical run to run. */
     S3_REDUCE_SEGMENTED = 0,
     /* contributions are added with warp-aggregated atomics; the FP32 path
      * keeps a two-sum compensation term per node that is folded in at the
@@ -96,7 +98,8 @@ typedef struct {
     int32_t build_ccss;    /* 1 = also build the CCSS forest (implied by layout = CCSS) */
     int32_t device;        /* CUDA device ordinal; -1 = the calling thread's current device */
     int32_t thread_max_w;  /* edges whose window N-|e|+1 is <= this use one thread per edge, wider ones
-                              one warp per edge; 0 = library default (32), range 1..32 */
+                              eight lanes (FP32) or one warp (FP64) per edge; 0 = library default (32),
+                              range 1..32 */
     int32_t block_threads; /* threads per block of the thread-per-edge kernels; 0 = default (128) */
     int32_t order;         /* order of the nodes inside every edge (the sequence the prefix products
                               and the CCSS forest follow) and of the edges inside a size bucket:
