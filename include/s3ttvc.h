@@ -111,7 +111,13 @@ typedef struct {
     int32_t small_bucket_edges; /* thread-per-edge buckets of size >= 2 with at most this many edges
                               share one fused launch (one edge per thread); 0 = default (40000),
                               negative = every bucket gets its own launch */
-    int32_t reserved[6];
+    int32_t closed_form_max_s; /* FP32/FP64 buckets of edges of size 2..this (at most 6) that run
+                              their own launch are evaluated in closed form -- the inclusion-exclusion
+                              expansion of E(x_v) prod_{u != v} Ebar(x_u) (Sec. II-A) -- where that
+                              costs fewer operations than the series products; every edge whose
+                              error bound (relative 2^-17 FP32, 2^-42 FP64) does not hold is
+                              recomputed by the series kernels.  0 = default (6), -1 = never */
+    int32_t reserved[5];
 } s3_options;
 
 typedef enum { S3_ORDER_DEGREE = 0, S3_ORDER_INDEX = 1 } s3_order;
@@ -207,6 +213,15 @@ s3_status s3_sttsvc_profile(s3_graph_t g, s3_dtype dt, const void *x, void *y, s
  * the handle's device.  reset != 0 clears the counter.  count: host.
  */
 s3_status s3_range_events(s3_graph_t g, int64_t *count, int32_t reset);
+
+/*
+ * Closed-form evaluation (s3_options.closed_form_max_s) on this handle:
+ * *buckets_f32 / *buckets_f64 = number of size buckets that use it for FP32 /
+ * FP64 calls; *rejected = edges that failed its error bound and went back to
+ * the series kernels, summed over all calls since the handle was built
+ * (synchronises the handle's device).  Any pointer may be NULL.  All host.
+ */
+s3_status s3_closed_form_query(s3_graph_t g, int32_t *buckets_f32, int32_t *buckets_f64, int64_t *rejected);
 
 /* ------------------------------------------------------------------ NQZ --- */
 

@@ -25,7 +25,8 @@ from ._lib import (S3_DF64, S3_F32, S3_F64, S3_LAYOUT_CCSS, S3_LAYOUT_EDGE, S3_R
 
 __all__ = [
     "Graph", "S3Error", "s3_options_init", "s3_format_inspect", "s3_build_format", "s3_graph_query",
-    "s3_sttsvc", "s3_sttsvc_layout", "s3_sttsvc_host", "s3_sttsvc_profile", "s3_range_events", "s3_hcentrality",
+    "s3_sttsvc", "s3_sttsvc_layout", "s3_sttsvc_host", "s3_sttsvc_profile", "s3_range_events", "s3_closed_form_query",
+    "s3_hcentrality",
     "s3_nqz_options_init", "s3_sttsvc_f32_noalloc", "s3_destroy", "s3_version", "lib_path",
     "Batch", "s3_batch_options_init", "s3_batch_create", "s3_sttsvc_batched", "s3_batch_autotune",
     "s3_batch_destroy", "MLP", "s3_features", "s3_mlp_create", "s3_mlp_get_params", "s3_mlp_forward",
@@ -175,6 +176,14 @@ def s3_range_events(g, reset=False):
     c = ctypes.c_int64()
     check(load().s3_range_events(g.handle, ctypes.byref(c), int(bool(reset))))
     return int(c.value)
+
+
+def s3_closed_form_query(g):
+    """(buckets evaluated in closed form for FP32 calls, for FP64 calls, edges
+    rejected by its error bound so far)."""
+    a, b, r = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int64()
+    check(load().s3_closed_form_query(g.handle, ctypes.byref(a), ctypes.byref(b), ctypes.byref(r)))
+    return int(a.value), int(b.value), int(r.value)
 
 
 def s3_nqz_options_init(**kw):

@@ -34,7 +34,8 @@ class s3_options(ctypes.Structure):
     _fields_ = [("rank", ctypes.c_int32), ("reduce", ctypes.c_int32), ("layout", ctypes.c_int32),
                 ("build_ccss", ctypes.c_int32), ("device", ctypes.c_int32), ("thread_max_w", ctypes.c_int32),
                 ("block_threads", ctypes.c_int32), ("order", ctypes.c_int32), ("streams", ctypes.c_int32),
-                ("small_bucket_edges", ctypes.c_int32), ("reserved", ctypes.c_int32 * 6)]
+                ("small_bucket_edges", ctypes.c_int32), ("closed_form_max_s", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 5)]
 
 
 class s3_format_info(ctypes.Structure):
@@ -95,6 +96,7 @@ SIGNATURES = {
     "s3_sttsvc_layout": (_I32, [_P, _I32, _I32, _P, _P, _P]),
     "s3_sttsvc_host": (_I32, [_P, _I32, _P, _P, _P]),
     "s3_range_events": (_I32, [_P, ctypes.POINTER(_I64), _I32]),
+    "s3_closed_form_query": (_I32, [_P, ctypes.POINTER(_I32), ctypes.POINTER(_I32), ctypes.POINTER(_I64)]),
     "s3_sttsvc_profile": (_I32, [_P, _I32, _P, _P, ctypes.POINTER(s3_profile), _P]),
     "s3_nqz_options_init": (_I32, [ctypes.POINTER(s3_nqz_options)]),
     "s3_hcentrality": (_I32, [_P, ctypes.POINTER(s3_nqz_options), _P, _P, ctypes.POINTER(s3_nqz_result), _P]),

@@ -72,6 +72,80 @@ void free_all(s3_graph_s *g) {
 
 }  // namespace
 
+// Closed-form evaluation of small buckets (s3_closed.cuh): which buckets use it,
+// their constants and rejected-edge lists.  A bucket qualifies for a call type when
+// it has its own launch, 2 <= s <= closed_form_max_s, 2 <= N-1 <= 127, its
+// series kernel takes lists (one thread per edge: W <= thread_max_w), the closed
+// form needs fewer operations than the series, and edges with equal x pass the
+// error gate with a margin of 2 (so that near-uniform inputs are not sent back).
+s3_status plan_closed_form(s3_graph_s *g) {
+    const size_t nb = g->buckets.size();
+    g->closed_mask.assign(nb, 0);
+    g->closed_args.assign(nb, ClosedArgs{});
+    const int max_s = g->opt.closed_form_max_s == 0 ? kClosedMaxS : std::min(g->opt.closed_form_max_s, kClosedMaxS);
+    const int tmw = (g->opt.thread_max_w <= 0 || g->opt.thread_max_w > 32) ? 32 : g->opt.thread_max_w;
+    const int n = g->N - 1;
+    int64_t list_len = 0;
+    std::vector<int64_t> list_off(nb, 0);
+    for (size_t k = 0; k < nb; ++k) {
+        const HostBucket &hb = g->buckets[k];
+        const int s = hb.s, W = g->N - s + 1;
+        if (max_s < 2 || s < 2 || s > max_s || n < 2 || n > 127 || hb.m <= 0 || g->in_tail[k] || W > tmw) continue;
+        int lg = 0;
+        while ((n >> (lg + 1)) != 0) ++lg;
+        // instructions per edge.  FP32: per subset a two-sum, the powering, its correction and
+        // the accumulations (~11 + 2 log2 n), per edge loads, scaling and stores (~40 + 20 s);
+        // the series kernels: their multiply-adds plus ~3 s W (the size-2 kernel has no products
+        // and little else).  FP64: the FP64 operations alone (the FP64 pipe is the bound).
+        const double subsets = std::ldexp(1.0, s) - 1.0, half = std::ldexp(1.0, s - 1);
+        const double series = s == 2 ? 5.0 * W : (2.0 * s - 5.0) * W * (W + 1) / 2.0 + 3.0 * s * W;
+        const double closed32 = subsets * (11.0 + 2.0 * lg) + s * half + 40.0 + 20.0 * s;
+        const double closed64 = subsets * (2.0 + 2.0 * lg) + s * half + 4.0;
+        // equal x: sum of |terms| over the signed sum, sum_j C(s-1,j) (j+1)^n
+        double pos = 0.0, sgn = 0.0, binom = 1.0;
+        for (int j = 0; j < s; ++j) {
+            const double t = binom * std::pow((double)(j + 1), (double)n);
+            pos += t;
+            sgn += ((s - 1 - j) & 1) ? -t : t;
+            binom = binom * (double)(s - 1 - j) / (double)(j + 1);
+        }
+        const double kappa = sgn > 0.0 ? pos / sgn : 1e300;
+        const double gate32 = ((double)n + half + 4.0) / 128.0;            // C 2^-24 / 2^-17
+        const double gate64 = ((double)s * n + half + 4.0) / 2048.0;       // C 2^-53 / 2^-42
+        int mask = 0;
+        if (closed32 < 0.8 * series && gate32 * kappa <= 0.5) mask |= 1;
+        if (closed64 < 0.8 * series && gate64 * kappa <= 0.5) mask |= 2;
+        if (!mask) continue;
+        g->closed_mask[k] = mask;
+        ClosedArgs &c = g->closed_args[k];
+        double fact = 1.0;  // (N-1)!
+        for (int i = 2; i <= n; ++i) fact *= (double)i;
+        c.Ki = g->K[k] / fact;
+        int e = 0;
+        c.Kim = (float)std::frexp(c.Ki, &e);
+        c.Kie = e;
+        list_off[k] = list_len;
+        list_len += hb.m;
+    }
+    if (list_len == 0) return S3_OK;
+    s3_status st;
+    if ((st = dev_alloc(g, &g->d_closed_list, (size_t)list_len)) != S3_OK) return st;
+    if ((st = dev_alloc(g, &g->d_closed_count, 4 * nb)) != S3_OK) return st;
+    if (cudaMemset(g->d_closed_count, 0, sizeof(int32_t) * 4 * nb) != cudaSuccess)
+        return cuda_fail(cudaGetLastError(), "memset");
+    for (size_t k = 0; k < nb; ++k) {
+        if (!g->closed_mask[k]) continue;
+        g->closed_args[k].fail_list = g->d_closed_list + list_off[k];
+        g->closed_args[k].fail_count = g->d_closed_count + 4 * k;
+        // the scheduler's cost of a closed-form bucket (FP32 estimate)
+        const double s = g->buckets[k].s;
+        g->bucket_cost[k] = (double)g->buckets[k].m * ((std::ldexp(1.0, (int)s) - 1.0) * 20.0 + 60.0 * s);
+    }
+    std::stable_sort(g->bucket_order.begin(), g->bucket_order.end(),
+                     [&](size_t a, size_t b) { return g->bucket_cost[a] > g->bucket_cost[b]; });
+    return S3_OK;
+}
+
 // Launch the per-bucket edge kernels and the reduce for one call.
 s3_status run_edges(s3_graph_s *g, s3_dtype dt, const void *x, void *y, int bias, const int32_t *skip,
                     cudaStream_t st, cudaEvent_t mid) {
@@ -92,6 +166,10 @@ s3_status run_edges(s3_graph_s *g, s3_dtype dt, const void *x, void *y, int bias
         S3_CUDA(cudaMemsetAsync(y, 0, esz * (size_t)g->n, st));
         if (dt == S3_F32) S3_CUDA(cudaMemsetAsync(g->d_comp, 0, sizeof(float) * (size_t)g->n, st));
     }
+    // the closed-form kernels append to lists that start empty: clear their lengths
+    // (one strided memset: the first counter of every bucket, running totals untouched)
+    if (g->d_closed_count && (dt == S3_F32 || dt == S3_F64))
+        S3_CUDA(cudaMemset2DAsync(g->d_closed_count, 4 * sizeof(int32_t), 0, sizeof(int32_t), g->buckets.size(), st));
     // fork: buckets run concurrently on the handle's streams (heaviest first, greedy balance)
     const int ns = g->n_streams;
     if (ns > 1) {
@@ -142,6 +220,21 @@ s3_status run_edges(s3_graph_s *g, s3_dtype dt, const void *x, void *y, int bias
         b.Ke = g->Ke[k];
         cudaStream_t bs = pick(g->bucket_cost[k]);
         const int tmw = g->opt.thread_max_w, bth = g->opt.block_threads;
+        const int closed_bit = dt == S3_F32 ? 1 : dt == S3_F64 ? 2 : 0;
+        if (g->closed_mask[k] & closed_bit) {
+            // closed form first; the series kernel then takes only the edges it rejected
+            ClosedArgs c = g->closed_args[k];
+            const HostBucket &cb = g->buckets[k];
+            const double half = std::ldexp(1.0, cb.s - 1);
+            c.gate = dt == S3_F32 ? ((double)(g->N - 1) + half + 4.0) / 128.0
+                                  : ((double)cb.s * (g->N - 1) + half + 4.0) / 2048.0;
+            cudaError_t ce = dt == S3_F32 ? launch_edge_closed_f32(b, (const float *)x, o, c, bs)
+                                          : launch_edge_closed_f64(b, (const double *)x, o, c, bs);
+            if (ce != cudaSuccess) return cuda_fail(ce, "closed-form launch");
+            ++launches;
+            b.list = c.fail_list;
+            b.count = c.fail_count;
+        }
         cudaError_t e = dt == S3_F32   ? launch_edge_bucket_f32(b, (const float *)x, o, tmw, bth, bs)
                         : dt == S3_F64 ? launch_edge_bucket_f64(b, (const double *)x, o, tmw, bth, bs)
                                        : launch_edge_bucket_df(b, (const double *)x, o, tmw, bth, bs);
@@ -224,6 +317,8 @@ s3_status s3_build_format(int64_t n, int64_t m, const int64_t *edge_ptr, const i
     if (o.thread_max_w < 0 || o.thread_max_w > 32) return fail(S3_EINVAL, "thread_max_w must be in 0..32");
     if (o.block_threads < 0 || o.block_threads > 256 || o.block_threads % 32) return fail(S3_EINVAL, "block_threads must be a multiple of 32 up to 256");
     if (o.streams < 0 || o.streams > 8) return fail(S3_EINVAL, "streams must be in 0..8");
+    if (o.closed_form_max_s < -1 || o.closed_form_max_s > kClosedMaxS)
+        return fail(S3_EINVAL, "closed_form_max_s must be in -1..6");
     if (o.order != S3_ORDER_DEGREE && o.order != S3_ORDER_INDEX) return fail(S3_EINVAL, "bad order");
     HostFormat f;
     try {
@@ -372,6 +467,7 @@ s3_status s3_build_format(int64_t n, int64_t m, const int64_t *edge_ptr, const i
             g->n_tail = (int32_t)tab.size();
         }
     }
+    if ((st = plan_closed_form(g)) != S3_OK) return bail(st);
     g->info.device_bytes = g->device_bytes;
     *out = g;
     return S3_OK;
@@ -457,6 +553,32 @@ s3_status s3_range_events(s3_graph_t g, int64_t *count, int32_t reset) {
     S3_CUDA(cudaMemcpy(&c, g->d_range, sizeof(c), cudaMemcpyDeviceToHost));
     *count = (int64_t)c;
     if (reset) S3_CUDA(cudaMemset(g->d_range, 0, sizeof(c)));
+    return S3_OK;
+}
+
+s3_status s3_closed_form_query(s3_graph_t g, int32_t *buckets_f32, int32_t *buckets_f64, int64_t *rejected) {
+    if (!g) return fail(S3_EINVAL, "graph is NULL");
+    int32_t n32 = 0, n64 = 0;
+    for (int32_t m : g->closed_mask) {
+        n32 += m & 1;
+        n64 += (m >> 1) & 1;
+    }
+    if (buckets_f32) *buckets_f32 = n32;
+    if (buckets_f64) *buckets_f64 = n64;
+    if (rejected) {
+        *rejected = 0;
+        if (g->d_closed_count) {
+            DeviceGuard guard(g->device);
+            S3_CUDA(cudaDeviceSynchronize());
+            std::vector<int32_t> cnt(4 * g->buckets.size());
+            S3_CUDA(cudaMemcpy(cnt.data(), g->d_closed_count, sizeof(int32_t) * cnt.size(), cudaMemcpyDeviceToHost));
+            for (size_t k = 0; k < g->buckets.size(); ++k) {
+                unsigned long long t = 0;
+                std::memcpy(&t, &cnt[4 * k + 2], sizeof(t));
+                *rejected += (int64_t)t;
+            }
+        }
+    }
     return S3_OK;
 }
 

@@ -96,6 +96,14 @@ struct s3_graph_s {
     int64_t tail_blocks = 0;
     size_t tail_smem[2] = {0, 0};       // dynamic shared memory of the launch (FP32, FP64)
     double tail_cost = 0.0;
+    // closed-form evaluation of small buckets: per bucket a bit mask of the call types
+    // that use it (1 = FP32, 2 = FP64) and its constants; d_closed_list holds every such
+    // bucket's rejected-edge list, d_closed_count four counters per bucket ([0] list
+    // length, cleared at the start of every call; [2..3] rejected edges in total)
+    std::vector<int32_t> closed_mask;
+    std::vector<s3::ClosedArgs> closed_args;
+    int32_t *d_closed_list = nullptr;
+    int32_t *d_closed_count = nullptr;
     std::vector<void *> allocations;
     int64_t device_bytes = 0;
 };

@@ -18,6 +18,23 @@ struct EdgeBucketArgs {
     double K;             // K(s,N) = s (N-1)! / (s! S(N,s))
     float Km;             // K = Km * 2^Ke with Km in [0.5, 1)
     int32_t Ke;
+    // list mode (the thread-per-edge and size-2 kernels): process only the bucket
+    // edges list[0 .. count[0]) instead of all m; count[2..3] is a running total of
+    // the list lengths
+    const int32_t *list;
+    int32_t *count;
+};
+
+// The closed-form (inclusion-exclusion) kernels of s3_closed.cuh.  Edges whose
+// error bound fails are appended to fail_list (bucket edge indices; fail_count[0]
+// entries) for the series kernels in list mode.
+struct ClosedArgs {
+    int32_t *fail_list;
+    int32_t *fail_count;
+    double Ki;            // K(s,N) / (N-1)!
+    float Kim;            // Ki = Kim * 2^Kie with Kim in [0.5, 1)
+    int32_t Kie;
+    double gate;          // an edge passes when every R_v > gate * sum_U |p_U|
 };
 
 // One small bucket of the fused small-bucket launch (device table, built once
@@ -76,6 +93,13 @@ cudaError_t launch_edge_group(const EdgeBucketArgs &b, const double *x, const Ed
                               int *launched);
 cudaError_t prepare_edge_group(float);
 cudaError_t prepare_edge_group(double);
+// Closed-form evaluation of one bucket (2 <= s <= 6, 2 <= N-1 <= 127); edges that
+// fail the error gate go to c.fail_list.  FP32 and FP64.
+cudaError_t launch_edge_closed_f32(const EdgeBucketArgs &b, const float *x, const EdgeOutArgs &o,
+                                   const ClosedArgs &c, cudaStream_t st);
+cudaError_t launch_edge_closed_f64(const EdgeBucketArgs &b, const double *x, const EdgeOutArgs &o,
+                                   const ClosedArgs &c, cudaStream_t st);
+constexpr int kClosedMaxS = 6;
 // One-time per-device set-up (shared-memory limits of the kernels).
 cudaError_t prepare_edge_kernels_f32();
 cudaError_t prepare_edge_kernels_f64();

@@ -452,6 +452,22 @@ __device__ __forceinline__ void edge_compute(const EdgeBucketArgs &b, const Edge
     if (nbad && o.range_events) atomicAdd(o.range_events, (unsigned long long)nbad);
 }
 
+// Edges a launch processes: all m of the bucket, or in list mode the count that
+// the closed-form kernel left (read once per thread, after that kernel finished).
+__device__ __forceinline__ int64_t list_length(const EdgeBucketArgs &b) {
+    return b.list ? min((int64_t)__ldcg(b.count), b.m) : b.m;
+}
+
+// List mode: the first thread of the grid adds the list's length to a running
+// total (count[2..3], 8-byte aligned).  The length itself is cleared before the
+// next call's closed-form launch.
+__device__ __forceinline__ void list_tally(const EdgeBucketArgs &b) {
+    if (b.list && blockIdx.x == 0 && threadIdx.x == 0) {
+        const int c = __ldcg(b.count);
+        if (c > 0) atomicAdd(reinterpret_cast<unsigned long long *>(b.count + 2), (unsigned long long)c);
+    }
+}
+
 // Shared memory per lane: Xb[2][s] and Pre[(s-2) W] of T, then Ib[3][s] member
 // ids and Sb[3][s] incidence slots (int32); 4-byte words.
 template <typename T>
@@ -484,12 +500,13 @@ __global__ void __launch_bounds__(256) edge_thread_kernel(EdgeBucketArgs b, cons
     int32_t *r0 = ibase, *r1 = ibase + ring, *r2 = ibase + 2 * ring;
     const int64_t stride = (int64_t)gridDim.x * BS;
     int64_t e = (int64_t)blockIdx.x * BS + tid;
-    if (e >= b.m) return;
+    const int64_t m = list_length(b);
+    list_tally(b);
     const int64_t ld = b.ld;
-    const int32_t *gid = b.ids + e;       // member 0 of edge e; member i at gid + i*ld
-    const int32_t *gsl = b.slot + e;
-
-    auto issue_ids = [&](const int32_t *gi, const int32_t *gs, int32_t *dst) {
+    // member i of bucket edge k sits at ids[i*ld + k]; in list mode the j-th edge is list[j]
+    auto edge_of = [&](int64_t j) -> int64_t { return b.list ? (int64_t)__ldg(b.list + j) : j; };
+    auto issue_ids = [&](int64_t k, int32_t *dst) {
+        const int32_t *gi = b.ids + k, *gs = b.slot + k;
         int32_t *d = dst;
         for (int i = 0; i < s; ++i) {
             cp_async<4>(d, gi);
@@ -503,29 +520,29 @@ __global__ void __launch_bounds__(256) edge_thread_kernel(EdgeBucketArgs b, cons
         for (int i = 0; i < s; ++i) cp_async<(int)sizeof(In)>(xb + i * kLS, x + src[i * kLS]);
     };
 
-    issue_ids(gid, gsl, r0);
-    cp_async_commit();
-    cp_async_wait_all();
-    issue_x(r0, xc);
-    if (e + stride < b.m) issue_ids(gid + stride, gsl + stride, r1);
-    cp_async_commit();
-    for (; e < b.m; e += stride) {
-        cp_async_wait_all();
-        if (e + stride < b.m) issue_x(r1, xn);
-        if (e + 2 * stride < b.m) issue_ids(gid + 2 * stride, gsl + 2 * stride, r2);
+    if (e < m) {
+        issue_ids(edge_of(e), r0);
         cp_async_commit();
-        edge_compute<T, W, BUF>(b, o, xc, Pre, r0, r0 + 3 * ring, s);
-        gid += stride;
-        gsl += stride;
-        int32_t *t = r0;
-        r0 = r1;
-        r1 = r2;
-        r2 = t;
-        In *tx = xc;
-        xc = xn;
-        xn = tx;
+        cp_async_wait_all();
+        issue_x(r0, xc);
+        if (e + stride < m) issue_ids(edge_of(e + stride), r1);
+        cp_async_commit();
+        for (; e < m; e += stride) {
+            cp_async_wait_all();
+            if (e + stride < m) issue_x(r1, xn);
+            if (e + 2 * stride < m) issue_ids(edge_of(e + 2 * stride), r2);
+            cp_async_commit();
+            edge_compute<T, W, BUF>(b, o, xc, Pre, r0, r0 + 3 * ring, s);
+            int32_t *t = r0;
+            r0 = r1;
+            r1 = r2;
+            r2 = t;
+            In *tx = xc;
+            xc = xn;
+            xn = tx;
+        }
+        cp_async_wait_all();
     }
-    cp_async_wait_all();
 }
 
 // Size-2 edges.  With P = Ebar(x_{v_1}) and Q = Ebar(x_{v_2}) on degrees 1..W
@@ -547,14 +564,17 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 2) edge_pair_kernel(
     constexpr int E = kPairEdges;
     const int64_t span = (int64_t)blockDim.x * E;
     const int64_t stride = (int64_t)gridDim.x * span;
+    const int64_t m = list_length(b);
+    list_tally(b);
     int nbad = 0;
-    for (int64_t e0 = (int64_t)blockIdx.x * span + threadIdx.x; e0 < b.m; e0 += stride) {
+    for (int64_t e0 = (int64_t)blockIdx.x * span + threadIdx.x; e0 < m; e0 += stride) {
         int v0[E], v1[E], t0[E], t1[E];
         In X0[E], X1[E];
 #pragma unroll
         for (int k = 0; k < E; ++k) {
-            const int64_t e = e0 + (int64_t)k * blockDim.x;
-            const bool in = e < b.m;
+            const int64_t j = e0 + (int64_t)k * blockDim.x;
+            const bool in = j < m;
+            const int64_t e = in && b.list ? (int64_t)__ldg(b.list + j) : j;
             v0[k] = in ? __ldg(b.ids + e) : 0;
             v1[k] = in ? __ldg(b.ids + b.ld + e) : 0;
             t0[k] = BUF ? (in ? __ldg(b.slot + e) : 0) : v0[k];
@@ -567,7 +587,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 2) edge_pair_kernel(
         }
 #pragma unroll
         for (int k = 0; k < E; ++k) {
-            if (e0 + (int64_t)k * blockDim.x >= b.m) break;
+            if (e0 + (int64_t)k * blockDim.x >= m) break;
             const int p = scale_exponent<In>(Arith<In>::absv(X0[k]) + Arith<In>::absv(X1[k]), b.target);
             const In g = Arith<In>::pow2(p);
             const In a0x = X0[k] * g, a1x = X1[k] * g;
