@@ -49,23 +49,31 @@ def measured_peaks():
     return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
 
 
-def algorithmic_counts(edges_per_size, N):
-    """FLOPs and HBM bytes of one FP32 S^3TTVc call by the edge-layout algorithm.
+def algorithmic_counts(edges_per_size, N, closed_sizes=()):
+    """FLOPs of one FP32 S^3TTVc call by the edge-layout algorithm.
 
-    Per edge of size s >= 2 with window W = N - s + 1:
+    Per edge of size s >= 2 with window W = N - s + 1 (series):
       Toeplitz products: (s-2) prefix + (s-3) suffix windows of W(W+1)/2 FMAs each
                          (s >= 3), plus W FMAs for the last suffix coefficient;
       dots: (W-1) for [t^(N-1)] F_e and W for each of the s-2 interior nodes;
       power tables: 2(s-1) tables of W coefficients, 2 multiplies per coefficient.
+    Per edge of a size in closed_sizes (inclusion-exclusion): for each of the 2^s - 1
+    subsets one add (its sum), floor(log2 n) + popcount(n) - 1 multiplies (sum^n,
+    n = N-1) and one add (the sum of |terms|), then s 2^(s-1) signed adds.  The
+    compensation of the FP32 subset sums is not counted.
     One FMA = 2 flops.  Size-1 edges: ~2 log2(N) multiplies.
     """
     fma = 0
     mul = 0
+    n = N - 1
     for s, cnt in enumerate(edges_per_size):
         if cnt == 0 or s == 0:
             continue
         if s == 1:
             mul += cnt * 2 * int(np.ceil(np.log2(max(N, 2))))
+            continue
+        if s in closed_sizes:
+            mul += cnt * ((2 ** s - 1) * (2 + n.bit_length() - 1 + bin(n).count("1") - 1) + s * 2 ** (s - 1))
             continue
         W = N - s + 1
         f = (W - 1) + max(s - 2, 0) * W
@@ -151,9 +159,12 @@ def dist_env():
     return ws, rank, local
 
 
-def make_workload():
+def make_workload(n=None):
+    """The power-law workload (n nodes, 5n edges; default the full size) and its x."""
     import s3synth
-    hg = s3synth.config_powerlaw(n=WORKLOAD["n"], m=WORKLOAD["m"], rank=WORKLOAD["rank"], seed=WORKLOAD["seed"])
+    n = n or WORKLOAD["n"]
+    m = WORKLOAD["m"] * n // WORKLOAD["n"]
+    hg = s3synth.config_powerlaw(n=n, m=m, rank=WORKLOAD["rank"], seed=WORKLOAD["seed"])
     # a centrality-like positive vector (degree^(1/(N-1)), rescaled to max 1), fixed seed jitter
     rng = np.random.default_rng(5)
     d = np.maximum(hg.degrees(), 1).astype(np.float64)
@@ -272,7 +283,8 @@ def run_gpu(args):
     prof = [s3.s3_sttsvc_profile(g, x, y) for _ in range(5)]
     edge_ms = float(np.mean([p["edge_ms"] for p in prof]))
     reduce_ms = float(np.mean([p["reduce_ms"] for p in prof]))
-    flops, fmas = algorithmic_counts(info["edges_per_size"], N)
+    closed = s3.s3_closed_form_query(g)
+    flops, fmas = algorithmic_counts(info["edges_per_size"], N, closed["f32"])
     peaks, peak_kind = measured_peaks()
     clocks = clk.summary()
     sm_max = clocks["sm_max_mhz"] or peaks.get("sm_max_mhz", 2070.0)
@@ -297,7 +309,8 @@ def run_gpu(args):
         "config": dict(WORKLOAD, x="degree^(1/24) jittered, max 1", reduce="segmented (deterministic)",
                        l2="inputs larger than L2: ids+slots+buffer = 16 bytes x 18.1M members",
                        nnz=nnz, parallelism=f"replicas x{ws}"),
-        "roofline": {"bound": "alu", "kernel": "per-edge series kernels (all size buckets of one call)",
+        "roofline": {"bound": "alu", "kernel": "per-edge kernels of one call: series products for all sizes but "
+                     + ",".join(map(str, closed["f32"])) + ", closed form for those",
                      "achieved": achieved_tflops, "peak": fp32_peak_tflops, "unit": "TFLOP/s",
                      "frac": achieved_tflops / fp32_peak_tflops, "traffic": traffic,
                      "peak_note": f"152 SMs x 128 FP32 lanes x 2 flops x {sm_max:.0f} MHz (max SM clock)",
@@ -563,12 +576,34 @@ def main():
     ap.add_argument("--batched", action="store_true", help="also time 64 graphs x 16 vectors batched vs single")
     ap.add_argument("--batched-scale", type=float, default=1.0)
     ap.add_argument("--warm-graphs", type=int, default=48, help="training hypergraphs of the warm start (0 = skip)")
+    ap.add_argument("--ncu-case", type=int, default=0, metavar="N",
+                    help="no timing: build the power-law workload at N nodes (5N edges) and make three "
+                         "FP32 calls, for ncu captures of a smaller case")
     args = ap.parse_args()
     global WARM_GRAPHS
     WARM_GRAPHS = args.warm_graphs
     if args.impl == "reference":
         return run_reference(args)
+    if args.ncu_case:
+        return ncu_case(args.ncu_case)
     return run_gpu(args)
+
+
+def ncu_case(n):
+    import torch
+
+    import paper_2311_08595_gb300 as s3
+    hg, x = make_workload(n)
+    g = s3.s3_build_format(hg.n, hg.edge_ptr, hg.members)
+    xd = torch.tensor(x, dtype=torch.float32, device="cuda")
+    yd = torch.empty_like(xd)
+    for _ in range(3):
+        s3.s3_sttsvc(g, xd, yd)
+    torch.cuda.synchronize()
+    print(json.dumps({"ncu_case": {"n": hg.n, "m": hg.m, "nnz": int(hg.edge_ptr[-1]),
+                                   "closed_form": s3.s3_closed_form_query(g), "sum_y": float(yd.double().sum())}}))
+    s3.s3_destroy(g)
+    return 0
 
 
 if __name__ == "__main__":

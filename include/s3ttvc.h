@@ -216,12 +216,13 @@ s3_status s3_range_events(s3_graph_t g, int64_t *count, int32_t reset);
 
 /*
  * Closed-form evaluation (s3_options.closed_form_max_s) on this handle:
- * *buckets_f32 / *buckets_f64 = number of size buckets that use it for FP32 /
- * FP64 calls; *rejected = edges that failed its error bound and went back to
- * the series kernels, summed over all calls since the handle was built
- * (synchronises the handle's device).  Any pointer may be NULL.  All host.
+ * *sizes_f32 / *sizes_f64 = bit mask of the edge sizes s (bit s) whose bucket
+ * uses it for FP32 / FP64 calls; *rejected = edges that failed its error bound
+ * and went back to the series kernels, summed over all calls since the handle
+ * was built (synchronises the handle's device).  Any pointer may be NULL.  All
+ * host.
  */
-s3_status s3_closed_form_query(s3_graph_t g, int32_t *buckets_f32, int32_t *buckets_f64, int64_t *rejected);
+s3_status s3_closed_form_query(s3_graph_t g, uint64_t *sizes_f32, uint64_t *sizes_f64, int64_t *rejected);
 
 /* ------------------------------------------------------------------ NQZ --- */
 

@@ -179,11 +179,12 @@ def s3_range_events(g, reset=False):
 
 
 def s3_closed_form_query(g):
-    """(buckets evaluated in closed form for FP32 calls, for FP64 calls, edges
-    rejected by its error bound so far)."""
-    a, b, r = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int64()
+    """Edge sizes evaluated in closed form for FP32 and for FP64 calls, and the edges
+    rejected by its error bound so far: {"f32": [s, ...], "f64": [...], "rejected": k}."""
+    a, b, r = ctypes.c_uint64(), ctypes.c_uint64(), ctypes.c_int64()
     check(load().s3_closed_form_query(g.handle, ctypes.byref(a), ctypes.byref(b), ctypes.byref(r)))
-    return int(a.value), int(b.value), int(r.value)
+    sizes = lambda m: [s for s in range(64) if (m >> s) & 1]
+    return {"f32": sizes(a.value), "f64": sizes(b.value), "rejected": int(r.value)}
 
 
 def s3_nqz_options_init(**kw):

@@ -96,7 +96,8 @@ SIGNATURES = {
     "s3_sttsvc_layout": (_I32, [_P, _I32, _I32, _P, _P, _P]),
     "s3_sttsvc_host": (_I32, [_P, _I32, _P, _P, _P]),
     "s3_range_events": (_I32, [_P, ctypes.POINTER(_I64), _I32]),
-    "s3_closed_form_query": (_I32, [_P, ctypes.POINTER(_I32), ctypes.POINTER(_I32), ctypes.POINTER(_I64)]),
+    "s3_closed_form_query": (_I32, [_P, ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_uint64),
+                                    ctypes.POINTER(_I64)]),
     "s3_sttsvc_profile": (_I32, [_P, _I32, _P, _P, ctypes.POINTER(s3_profile), _P]),
     "s3_nqz_options_init": (_I32, [ctypes.POINTER(s3_nqz_options)]),
     "s3_hcentrality": (_I32, [_P, ctypes.POINTER(s3_nqz_options), _P, _P, ctypes.POINTER(s3_nqz_result), _P]),

@@ -556,15 +556,16 @@ s3_status s3_range_events(s3_graph_t g, int64_t *count, int32_t reset) {
     return S3_OK;
 }
 
-s3_status s3_closed_form_query(s3_graph_t g, int32_t *buckets_f32, int32_t *buckets_f64, int64_t *rejected) {
+s3_status s3_closed_form_query(s3_graph_t g, uint64_t *sizes_f32, uint64_t *sizes_f64, int64_t *rejected) {
     if (!g) return fail(S3_EINVAL, "graph is NULL");
-    int32_t n32 = 0, n64 = 0;
-    for (int32_t m : g->closed_mask) {
-        n32 += m & 1;
-        n64 += (m >> 1) & 1;
+    uint64_t m32 = 0, m64 = 0;
+    for (size_t k = 0; k < g->closed_mask.size(); ++k) {
+        const uint64_t bit = 1ull << g->buckets[k].s;  // s <= kClosedMaxS for these buckets
+        if (g->closed_mask[k] & 1) m32 |= bit;
+        if (g->closed_mask[k] & 2) m64 |= bit;
     }
-    if (buckets_f32) *buckets_f32 = n32;
-    if (buckets_f64) *buckets_f64 = n64;
+    if (sizes_f32) *sizes_f32 = m32;
+    if (sizes_f64) *sizes_f64 = m64;
     if (rejected) {
         *rejected = 0;
         if (g->d_closed_count) {

@@ -35,10 +35,10 @@
 
 namespace s3 {
 
-// Edges per thread whose loads are in flight together: more for the small sizes,
-// which are bound by load latency, fewer where the subset sums need the registers.
+// Edges per thread whose loads are in flight together (measured: four for size 2,
+// two for sizes 3 and 4, one from size 5 on, where the subset sums need the registers).
 template <int S> struct ClosedShape {
-    static constexpr int E = S <= 3 ? 4 : S == 4 ? 2 : 1;
+    static constexpr int E = S <= 2 ? 4 : S <= 4 ? 2 : 1;
 };
 
 // h^n for n = 2^NB + (lower NB bits): left-to-right binary powering, NB

@@ -34,9 +34,9 @@ def run(hg, x, dtype, calls=1, **opts):
         s3.s3_sttsvc(g, xd, yd)
         torch.cuda.synchronize()
         outs.append(yd.double().cpu().numpy())
-    info = s3.s3_closed_form_query(g)
+    q = s3.s3_closed_form_query(g)
     s3.s3_destroy(g)
-    return outs, info
+    return outs, (q["f32"], q["f64"], q["rejected"])
 
 
 @pytest.fixture(scope="module")
@@ -57,20 +57,20 @@ def test_closed_form_matches_oracle(powerlaw):
             (y,), (b32, b64, rej) = run(hg, x, dt, reduce=red, small_bucket_edges=-1)
             # FP32: sizes 3..5 (size 2 keeps its lean series kernel, size 6 is cheaper as series);
             # FP64: sizes 2..6
-            assert (b32, b64) == (3, 5), (b32, b64)
+            assert (b32, b64) == ([3, 4, 5], [2, 3, 4, 5, 6]), (b32, b64)
             assert rej == 0, f"{dt}: {rej} edges rejected for a near-uniform vector"
             e = rel_err(y, want)
             assert e <= tol, f"{dt} reduce={red}: {e:.3e}"
     # the series path alone agrees to within both paths' error
     (y_off,), (b32, b64, _) = run(hg, x, "f64", small_bucket_edges=-1, closed_form_max_s=-1)
-    assert b32 == 0 and b64 == 0
+    assert b32 == [] and b64 == []
     assert rel_err(y_off, want) <= F64_TOL
 
 
 def test_closed_form_sizes_limited(powerlaw):
     hg, x = powerlaw
     (y,), (b32, b64, _) = run(hg, x, "f32", small_bucket_edges=-1, closed_form_max_s=3)
-    assert (b32, b64) == (1, 2)
+    assert (b32, b64) == ([3], [2, 3])
     assert rel_err(y, oracle.ttsv1(hg, x)) <= F32_TOL
 
 
@@ -111,7 +111,7 @@ def test_default_launch_plan_uses_closed_form():
     hg = s3synth.config_powerlaw(n=20000, m=100000, rank=25, seed=11)
     x = s3synth.x_uniform(hg.n, 0.5, 1.5, 11)
     (y,), (b32, b64, rej) = run(hg, x, "f32")
-    assert (b32, b64) == (0, 1) and rej == 0   # the size-2 bucket, FP64 only
+    assert (b32, b64) == ([], [2]) and rej == 0   # the size-2 bucket, FP64 only
     assert rel_err(y, oracle.ttsv1(hg, x)) <= F32_TOL
 
 
@@ -119,4 +119,4 @@ def test_low_rank_keeps_series():
     # at rank 5 the series is cheaper than 2^s subsets: no bucket uses the closed form
     hg = s3synth.config_small(seed=1)
     (_,), (b32, b64, _) = run(hg, s3synth.x_uniform(hg.n, 0.0, 1.0, 1), "f32", small_bucket_edges=-1)
-    assert b32 == 0 and b64 == 0
+    assert b32 == [] and b64 == []
