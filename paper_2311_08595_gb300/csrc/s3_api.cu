@@ -560,6 +560,7 @@ s3_status s3_closed_form_query(s3_graph_t g, uint64_t *sizes_f32, uint64_t *size
     if (!g) return fail(S3_EINVAL, "graph is NULL");
     uint64_t m32 = 0, m64 = 0;
     for (size_t k = 0; k < g->closed_mask.size(); ++k) {
+        if (!g->closed_mask[k]) continue;
         const uint64_t bit = 1ull << g->buckets[k].s;  // s <= kClosedMaxS for these buckets
         if (g->closed_mask[k] & 1) m32 |= bit;
         if (g->closed_mask[k] & 2) m64 |= bit;
