@@ -175,7 +175,11 @@ s3_status s3_graph_query(s3_graph_t g, s3_format_info *info);
  * rescaled by an exact power of two before the products and the result is
  * rescaled back, so intermediate terms stay in range.  Results that underflow
  * or overflow dt are counted (s3_range_events) but not reported here.
- * Uses the handle's layout and reduce mode.
+ * Small edges may be evaluated in closed form (s3_options.closed_form_max_s)
+ * within its stated error bound.  Uses the handle's layout and reduce mode.
+ * Calls on one handle share its scratch memory (reduce buffer, closed-form
+ * lists): calls that could run at the same time on the GPU (unordered
+ * streams) must use different handles.
  */
 s3_status s3_sttsvc(s3_graph_t g, s3_dtype dt, const void *x, void *y, void *stream);
 
