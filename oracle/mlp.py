@@ -3,8 +3,10 @@
 Restates, in plain numpy, the warm-start network as its C interface documents
 it: per-node features, the 12-64-64-1 ReLU MLP evaluated with
 BF16-rounded weights, the mean-squared loss, its gradient, and one Adam step.
-The gradient is pinned by central finite differences of the loss
-(tests/test_oracle_mlp.py), the features by a direct loop over the edges.
+Pins (tests/test_oracle_mlp.py): the forward pass, the loss and the output
+layer's gradient against values worked out by hand for a small hand-set
+network; the full gradient by central finite differences of the loss; Adam
+over two steps against a hand computation; the features by hand on Fig. 1.
 """
 from __future__ import annotations
 

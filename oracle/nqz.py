@@ -1,19 +1,17 @@
 """Algorithm 1 (NQZ) in FP64 -- test infrastructure only.
 
 The H-eigenvector centrality is the positive x with B x^(N-1) = lambda x^[N-1]
-(Sec. II).  Algorithm 1 as printed:
+(Sec. II).  Algorithm 1 finds it by a normalised power iteration: starting from
+the uniform vector 1/n it applies S^3TTVc, takes the entrywise (N-1)-th root of
+the result and rescales it to unit 1-norm; the ratios z_v / x_v^(N-1) of the
+next S^3TTVc output z to the current iterate bracket the eigenvalue, and the
+iteration stops once (largest ratio - smallest ratio) / smallest ratio falls
+below the tolerance.
 
-    y = 1/n * ones;  z = TTSV1(H, y)
-    repeat
-        x = z^[1/(N-1)] / || z^[1/(N-1)] ||_1
-        z = TTSV1(H, x)
-        lambda_min = min(z ./ x^[N-1]);  lambda_max = max(z ./ x^[N-1])
-    until (lambda_max - lambda_min) / lambda_min < tau
-
-The iteration count returned is the number of passes through the repeat body.
-``x0`` replaces the uniform start when given (the warm start of the learned
-model; any positive start works because TTSV1 is homogeneous of degree N-1 and
-the first pass normalises).
+The iteration count returned is the number of power steps taken (each one
+S^3TTVc call after the initial one).  ``x0`` replaces the uniform start when
+given (the warm start of the learned model; any positive start works because
+S^3TTVc is homogeneous of degree N-1 and the first step normalises).
 """
 from __future__ import annotations
 
