@@ -84,11 +84,24 @@ def algorithmic_counts(edges_per_size, N, closed_sizes=()):
     return 2 * fma + mul, fma
 
 
-def hbm_bytes(nnz, n, n_small, esz=4):
-    """Algorithmic HBM bytes of one call: member ids + incidence slots read, the
-    per-(edge,node) buffer written and read back by the reduce, x gathered once,
-    y written, the node lists and incidence pointers of the reduce."""
-    return 4 * nnz + 4 * nnz + esz * nnz * 2 + esz * n + esz * n + 8 * (n + 1) + 4 * n
+def hbm_bytes(nnz, n, esz=4, deterministic=True, comp=False):
+    """Algorithmic HBM bytes of one call by the survey's count: the int32 member ids
+    (4 per member), x gathered once and y written (esz per node each), the FP32
+    compensation vector in atomic mode (4 per node), and, in deterministic mode, the
+    per-(edge, node) buffer written by the edge kernels and read back by the reduce
+    (2 esz per member)."""
+    b = 4 * nnz + 2 * esz * n
+    if comp:
+        b += 4 * n
+    if deterministic:
+        b += 2 * esz * nnz
+    return b
+
+
+def layout_bytes(nnz, n):
+    """Bytes the layout adds on top of hbm_bytes: the incidence-slot index of every
+    member (4 per member) and the reduce's node lists and offsets (about 12 per node)."""
+    return 4 * nnz + 12 * n
 
 
 class ClockSampler:
@@ -165,11 +178,8 @@ def make_workload(n=None):
     n = n or WORKLOAD["n"]
     m = WORKLOAD["m"] * n // WORKLOAD["n"]
     hg = s3synth.config_powerlaw(n=n, m=m, rank=WORKLOAD["rank"], seed=WORKLOAD["seed"])
-    # a centrality-like positive vector (degree^(1/(N-1)), rescaled to max 1), fixed seed jitter
-    rng = np.random.default_rng(5)
-    d = np.maximum(hg.degrees(), 1).astype(np.float64)
-    x = d ** (1.0 / (hg.rank - 1)) * rng.uniform(0.9, 1.1, hg.n)
-    return hg, x / x.max()
+    # a centrality-like positive vector (degree^(1/(N-1)) jittered, max 1)
+    return hg, s3synth.x_degree_like(hg, seed=5)
 
 
 # ------------------------------------------------------------ CPU oracle ---
@@ -246,7 +256,7 @@ def run_gpu(args):
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
 
-    hg, x_np = make_workload()
+    hg, x_np = make_workload(args.n or None)
     g = s3.s3_build_format(hg.n, hg.edge_ptr, hg.members)
     info = s3.s3_graph_query(g)
     N, nnz, n = info["rank"], info["nnz"], info["n"]
@@ -280,17 +290,20 @@ def run_gpu(args):
     launches = s3.s3_sttsvc_profile(g, x, y)["launches"]
 
     # phase split (device events inside the library), averaged
-    prof = [s3.s3_sttsvc_profile(g, x, y) for _ in range(5)]
+    prof = [s3.s3_sttsvc_profile(g, x, y) for _ in range(20)]
     edge_ms = float(np.mean([p["edge_ms"] for p in prof]))
     reduce_ms = float(np.mean([p["reduce_ms"] for p in prof]))
     closed = s3.s3_closed_form_query(g)
     flops, fmas = algorithmic_counts(info["edges_per_size"], N, closed["f32"])
     peaks, peak_kind = measured_peaks()
     clocks = clk.summary()
-    sm_max = clocks["sm_max_mhz"] or peaks.get("sm_max_mhz", 2070.0)
-    fp32_peak_tflops = 152 * 128 * 2 * sm_max * 1e6 / 1e12
+    # measured FMA peaks of this device (FP32, FP64), clocks sampled while they run
+    with ClockSampler(local) as pclk:
+        p32 = s3.s3_fma_peak(fp64=False, reps=50)
+        p64 = s3.s3_fma_peak(fp64=True, reps=20)
+    pclocks = pclk.summary()
     achieved_tflops = flops / (edge_ms * 1e-3) / 1e12
-    bytes_call = hbm_bytes(nnz, n, 0)
+    bytes_call = hbm_bytes(nnz, n)
     # DRAM traffic of the edge kernels of one call, from the committed ncu capture -- only while
     # the kernel sources are the ones it was taken with
     traffic = None
@@ -306,44 +319,48 @@ def run_gpu(args):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
         "warmup": max(args.warmup, 3), "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": dict(WORKLOAD, x="degree^(1/24) jittered, max 1", reduce="segmented (deterministic)",
-                       l2="inputs larger than L2: ids+slots+buffer = 16 bytes x 18.1M members",
+        "config": dict(WORKLOAD, n=n, m=info["m"], x="degree^(1/24) jittered, max 1",
+                       reduce="segmented (deterministic)",
+                       l2="inputs larger than L2: ids+slots+buffer = 16 bytes x members" if nnz > 8_000_000
+                       else "inputs smaller than L2 (reduced workload)",
                        nnz=nnz, parallelism=f"replicas x{ws}"),
         "roofline": {"bound": "alu", "kernel": "per-edge kernels of one call: series products for all sizes but "
                      + ",".join(map(str, closed["f32"])) + ", closed form for those",
-                     "achieved": achieved_tflops, "peak": fp32_peak_tflops, "unit": "TFLOP/s",
-                     "frac": achieved_tflops / fp32_peak_tflops, "traffic": traffic,
-                     "peak_note": f"152 SMs x 128 FP32 lanes x 2 flops x {sm_max:.0f} MHz (max SM clock)",
-                     "algorithmic_flops_per_call": flops, "edge_ms": edge_ms, "reduce_ms": reduce_ms},
+                     "achieved": achieved_tflops, "peak": p32["tflops"], "unit": "TFLOP/s",
+                     "frac": achieved_tflops / p32["tflops"], "traffic": traffic,
+                     "peak_note": "of measured: FP32 FMA-chain probe (s3_fma_peak) on this device, "
+                                  f"{p32['sm_count']} SMs, median SM clock {pclocks['sm_mhz']} MHz during the probe",
+                     "algorithmic_flops_per_call": flops, "edge_ms": edge_ms, "reduce_ms": reduce_ms,
+                     "edge_ms_x_sm_mhz": edge_ms * (clocks["sm_mhz"] or 0.0)},
         "hbm": {"algorithmic_bytes_per_call": bytes_call, "achieved_gbs": bytes_call / (ms * 1e-3) / 1e9,
                 "peak_gbs": peaks["hbm_gbs"], "frac": bytes_call / (ms * 1e-3) / 1e9 / peaks["hbm_gbs"],
-                "peak_kind": peak_kind},
+                "peak_kind": peak_kind, "layout_bytes_per_call": layout_bytes(nnz, n),
+                "count": "4 B ids per member + x and y + 8 B per member buffer write+read (deterministic mode)"},
+        "fma_peaks": {"fp32_tflops": p32["tflops"], "fp64_tflops": p64["tflops"], "sm_count": p32["sm_count"],
+                      "threads_per_sm": p32["threads_per_sm"], "rated_clock_mhz": p32["clock_mhz"],
+                      "clocks_during_probe": pclocks},
         "clocks": clocks, "gpu_launches": launches * args.steps,
     }
-    # FP64 S^3TTVc
+    # FP64 S^3TTVc (event-timed over 20 calls), with its roofline against the FP64 FMA peak
     x64, y64 = x.double(), torch.empty(n, dtype=torch.float64, device=dev)
-    s3.s3_sttsvc(g, x64, y64)
-    torch.cuda.synchronize()
-    st64 = time.perf_counter()
-    reps64 = 3
-    for _ in range(reps64):
-        s3.s3_sttsvc(g, x64, y64)
-    torch.cuda.synchronize()
-    ms64 = (time.perf_counter() - st64) * 1e3 / reps64
-    out["fp64"] = {"value": nnz / (ms64 * 1e-3), "unit": UNIT, "ms_per_call": ms64,
-                   "fp32_speedup": ms64 / ms}
+    ms64 = _time_calls(g, x64, y64, 20)
+    prof64 = [s3.s3_sttsvc_profile(g, x64, y64) for _ in range(3)]
+    edge64 = float(np.mean([p["edge_ms"] for p in prof64]))
+    flops64, _ = algorithmic_counts(info["edges_per_size"], N, closed["f64"])
+    out["fp64"] = {"value": nnz / (ms64 * 1e-3), "unit": UNIT, "ms_per_call": ms64, "calls_timed": 20,
+                   "fp32_speedup": ms64 / ms,
+                   "roofline": {"bound": "alu", "achieved": flops64 / (edge64 * 1e-3) / 1e12, "peak": p64["tflops"],
+                                "unit": "TFLOP/s", "frac": flops64 / (edge64 * 1e-3) / 1e12 / p64["tflops"],
+                                "edge_ms": edge64, "closed_form_sizes": closed["f64"],
+                                "peak_note": "of measured: FP64 FMA-chain probe (s3_fma_peak)"},
+                   "hbm_bytes_per_call": hbm_bytes(nnz, n, esz=8)}
     # FP64 in and out with the series in double-float (pairs of FP32)
     ydf = torch.empty_like(y64)
-    s3.s3_sttsvc(g, x64, ydf, df=True)
-    torch.cuda.synchronize()
-    stdf = time.perf_counter()
-    for _ in range(reps64):
-        s3.s3_sttsvc(g, x64, ydf, df=True)
-    torch.cuda.synchronize()
-    msdf = (time.perf_counter() - stdf) * 1e3 / reps64
+    msdf = _time_calls(g, x64, ydf, 20, df=True)
     a, b = ydf.cpu().numpy(), y64.cpu().numpy()
     nz = b != 0
-    out["df64"] = {"value": nnz / (msdf * 1e-3), "unit": UNIT, "ms_per_call": msdf, "speedup_vs_fp64": ms64 / msdf,
+    out["df64"] = {"value": nnz / (msdf * 1e-3), "unit": UNIT, "ms_per_call": msdf, "calls_timed": 20,
+                   "speedup_vs_fp64": ms64 / msdf,
                    "max_rel_diff_vs_fp64": float(np.max(np.abs(a[nz] - b[nz]) / np.abs(b[nz])))}
     # end to end through the host-buffer entry point
     xh = x.cpu().pin_memory()
@@ -355,6 +372,8 @@ def run_gpu(args):
     e2e_ms = (time.perf_counter() - t0) * 1e3 / args.steps
     out["e2e"] = {"value": nnz * ws / (e2e_ms * 1e-3), "unit": UNIT, "ms_per_step": e2e_ms,
                   "h2d_bytes_per_step": 4 * n, "d2h_bytes_per_step": 4 * n}
+    if rank == 0 and ws == 1 and not args.skip_extras:
+        out["small_fp64"] = small_config(dev)
 
     if rank == 0 and ws == 1 and (args.batched or not args.skip_extras):
         out["batched"] = batched(dev, scale=args.batched_scale)
@@ -449,20 +468,48 @@ def warm_start(lcc, dev, graphs=48, n=50000, epochs=20):
     return out
 
 
-def _time_calls(g, x, y, reps):
+def _time_calls(g, x, y, reps, df=False):
+    """Device time per s3_sttsvc call (CUDA events on the current stream), after one warm-up call."""
     import torch
 
     import paper_2311_08595_gb300 as s3
-    s3.s3_sttsvc(g, x, y)
+    s3.s3_sttsvc(g, x, y, df=df)
     torch.cuda.synchronize()
     st = torch.cuda.current_stream()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(st)
     for _ in range(reps):
-        s3.s3_sttsvc(g, x, y)
+        s3.s3_sttsvc(g, x, y, df=df)
     e1.record(st)
     torch.cuda.synchronize()
     return e0.elapsed_time(e1) / reps
+
+
+def small_config(dev, calls=2000):
+    """The small single-call case: n=1000, m=5000, sizes U{2..5} (rank 5), x ~ U(0,1), FP64,
+    one S^3TTVc call at a time (launch-latency bound); event-timed over `calls` calls, and the
+    result against the CPU oracle on every node."""
+    import torch
+
+    import oracle
+    import paper_2311_08595_gb300 as s3
+    import s3synth
+    hg = s3synth.config_small(seed=1)
+    x_np = s3synth.x_uniform(hg.n, 0.0, 1.0, 1)
+    g = s3.s3_build_format(hg.n, hg.edge_ptr, hg.members)
+    x = torch.tensor(x_np, dtype=torch.float64, device=dev)
+    y = torch.empty_like(x)
+    ms = _time_calls(g, x, y, calls)
+    info = s3.s3_graph_query(g)
+    want = oracle.ttsv1(hg, x_np)
+    err = float(np.max(np.abs(y.cpu().numpy() - want) / np.abs(want)))
+    out = {"workload": "small n=1000 m=5000 sizes U{2..5} rank 5, x~U(0,1), FP64", "nnz": hg.nnz,
+           "ms_per_call": ms, "members_per_s": hg.nnz / (ms * 1e-3), "calls_timed": calls,
+           "launches_per_call": s3.s3_sttsvc_profile(g, x, y)["launches"],
+           "max_rel_err_vs_oracle": err, "hbm_bytes_per_call": hbm_bytes(hg.nnz, hg.n, esz=8),
+           "edges_per_size": info["edges_per_size"][:6]}
+    s3.s3_destroy(g)
+    return out
 
 
 def large_rank(dev, sample=300):
@@ -480,8 +527,8 @@ def large_rank(dev, sample=300):
     x64 = torch.tensor(x_np, dtype=torch.float64, device=dev)
     x32 = x64.float()
     y64, y32 = torch.empty_like(x64), torch.empty_like(x32)
-    ms32 = _time_calls(g, x32, y32, 3)
-    ms64 = _time_calls(g, x64, y64, 2)
+    ms32 = _time_calls(g, x32, y32, 20)
+    ms64 = _time_calls(g, x64, y64, 20)
     a, b = y32.double().cpu().numpy(), y64.cpu().numpy()
     d = hg.degrees()
     rel = np.abs(a - b)[d > 0] / np.abs(b)[d > 0]
@@ -490,7 +537,7 @@ def large_rank(dev, sample=300):
     e64 = float(np.max(np.abs(b[nodes] - want) / np.abs(want)))
     s3.s3_destroy(g)
     return {"workload": "largerank n=200k m=1M geometric(0.1) sizes on 2..100, x~U(0.5,1.5)", "nnz": hg.nnz,
-            "fp32_ms": ms32, "fp64_ms": ms64, "fp32_members_per_s": hg.nnz / (ms32 * 1e-3),
+            "fp32_ms": ms32, "fp64_ms": ms64, "calls_timed": 20, "fp32_members_per_s": hg.nnz / (ms32 * 1e-3),
             "fp64_members_per_s": hg.nnz / (ms64 * 1e-3), "fp32_speedup": ms64 / ms32,
             "fp32_rel_err_per_node": {"max": float(rel.max()), "median": float(np.median(rel)),
                                       "p99": float(np.quantile(rel, 0.99))},
@@ -576,34 +623,14 @@ def main():
     ap.add_argument("--batched", action="store_true", help="also time 64 graphs x 16 vectors batched vs single")
     ap.add_argument("--batched-scale", type=float, default=1.0)
     ap.add_argument("--warm-graphs", type=int, default=48, help="training hypergraphs of the warm start (0 = skip)")
-    ap.add_argument("--ncu-case", type=int, default=0, metavar="N",
-                    help="no timing: build the power-law workload at N nodes (5N edges) and make three "
-                         "FP32 calls, for ncu captures of a smaller case")
+    ap.add_argument("--n", type=int, default=0, metavar="N",
+                    help="nodes of the power-law workload (5N edges; default 1,000,000)")
     args = ap.parse_args()
     global WARM_GRAPHS
     WARM_GRAPHS = args.warm_graphs
     if args.impl == "reference":
         return run_reference(args)
-    if args.ncu_case:
-        return ncu_case(args.ncu_case)
     return run_gpu(args)
-
-
-def ncu_case(n):
-    import torch
-
-    import paper_2311_08595_gb300 as s3
-    hg, x = make_workload(n)
-    g = s3.s3_build_format(hg.n, hg.edge_ptr, hg.members)
-    xd = torch.tensor(x, dtype=torch.float32, device="cuda")
-    yd = torch.empty_like(xd)
-    for _ in range(3):
-        s3.s3_sttsvc(g, xd, yd)
-    torch.cuda.synchronize()
-    print(json.dumps({"ncu_case": {"n": hg.n, "m": hg.m, "nnz": int(hg.edge_ptr[-1]),
-                                   "closed_form": s3.s3_closed_form_query(g), "sum_y": float(yd.double().sum())}}))
-    s3.s3_destroy(g)
-    return 0
 
 
 if __name__ == "__main__":

@@ -53,8 +53,9 @@ typedef enum {
     S3_ENOMEM = 2,    /* device or host allocation failed */
     S3_ECUDA = 3,     /* a CUDA call failed (message in s3_last_error) */
     S3_ENOCONV = 4,   /* NQZ did not reach the tolerance within max_iter */
-    S3_ETIMEOUT = 5,  /* a bounded device wait gave up */
-    S3_ERANGE = 6,    /* results left the range of the arithmetic type */
+    /* 5 is unused: no kernel of the library waits on a flag, a peer or a barrier */
+    S3_ERANGE = 6,    /* results left the range of the arithmetic type (synchronous and
+                         range-checked calls, s3_options.range_check) */
     S3_ENOTSUP = 7    /* configuration not supported by this build */
 } s3_status;
 
@@ -117,7 +118,14 @@ typedef struct {
                               costs fewer operations than the series products; every edge whose
                               error bound (relative 2^-17 FP32, 2^-42 FP64) does not hold is
                               recomputed by the series kernels.  0 = default (6), -1 = never */
-    int32_t reserved[5];
+    int32_t range_check;   /* 1 = s3_sttsvc / s3_sttsvc_layout read the handle's range counter
+                              (s3_range_events) on the call's stream before and after the call,
+                              synchronise that stream and return S3_ERANGE when this call's
+                              results left the normal range of the call's type (y is still
+                              written).  Not allowed while the stream is being captured into a
+                              CUDA graph (S3_ENOTSUP).  0 = default: asynchronous, such results
+                              are only counted */
+    int32_t reserved[4];
 } s3_options;
 
 typedef enum { S3_ORDER_DEGREE = 0, S3_ORDER_INDEX = 1 } s3_order;
@@ -173,8 +181,11 @@ s3_status s3_graph_query(s3_graph_t g, s3_format_info *info);
  * y: device, n elements of dt, overwritten.  x and y must not overlap.
  * Arithmetic is in dt throughout the series products; per edge the vector is
  * rescaled by an exact power of two before the products and the result is
- * rescaled back, so intermediate terms stay in range.  Results that underflow
- * or overflow dt are counted (s3_range_events) but not reported here.
+ * rescaled back, so intermediate terms stay in range.  Per-(edge, node)
+ * results that underflow or overflow dt are counted on the device
+ * (s3_range_events).  By default the call stays asynchronous and does not
+ * report them; a handle built with s3_options.range_check = 1 synchronises
+ * the stream and returns S3_ERANGE when this call produced any (y written).
  * Small edges may be evaluated in closed form (s3_options.closed_form_max_s)
  * within its stated error bound.  Uses the handle's layout and reduce mode.
  * Calls on one handle share its scratch memory (reduce buffer, closed-form
@@ -190,6 +201,8 @@ s3_status s3_sttsvc_layout(s3_graph_t g, s3_dtype dt, int32_t layout, const void
  * End-to-end variant: x_host and y_host are HOST buffers (n elements of dt,
  * pinned memory recommended).  Copies x to the device, computes as
  * s3_sttsvc, copies y back and synchronises ``stream`` before returning.
+ * Being synchronous it always checks the range counter: S3_ERANGE (y_host
+ * written) when a result of this call left the normal range of dt.
  */
 s3_status s3_sttsvc_host(s3_graph_t g, s3_dtype dt, const void *x_host, void *y_host, void *stream);
 
@@ -213,8 +226,9 @@ s3_status s3_sttsvc_profile(s3_graph_t g, s3_dtype dt, const void *x, void *y, s
 /*
  * Number of per-(edge, node) results since the handle was built (or since the
  * last reset) that came out as zero, subnormal or non-finite although their
- * exact value is a positive normal number of the call's type.  Synchronises
- * the handle's device.  reset != 0 clears the counter.  count: host.
+ * exact value is a positive normal number of the call's type.  Waits for the
+ * handle's last call (an event recorded on that call's stream), not for the
+ * rest of the device.  reset != 0 clears the counter.  count: host.
  */
 s3_status s3_range_events(s3_graph_t g, int64_t *count, int32_t reset);
 
@@ -223,7 +237,7 @@ s3_status s3_range_events(s3_graph_t g, int64_t *count, int32_t reset);
  * *sizes_f32 / *sizes_f64 = bit mask of the edge sizes s (bit s) whose bucket
  * uses it for FP32 / FP64 calls; *rejected = edges that failed its error bound
  * and went back to the series kernels, summed over all calls since the handle
- * was built (synchronises the handle's device).  Any pointer may be NULL.  All
+ * was built (waits for the handle's last call only).  Any pointer may be NULL.  All
  * host.
  */
 s3_status s3_closed_form_query(s3_graph_t g, uint64_t *sizes_f32, uint64_t *sizes_f64, int64_t *rejected);
@@ -425,6 +439,28 @@ s3_status s3_mlp_destroy(s3_mlp_t m);
  */
 s3_status s3_sttsvc_f32_noalloc(int64_t n, int64_t m, int32_t rank, const int64_t *edge_ptr,
                                 const int32_t *members, const float *x, float *y, void *stream);
+
+/* --------------------------------------------------------- measurement --- */
+
+typedef struct {
+    double tflops;            /* multiply-add throughput, 2 flops per FMA */
+    double flops_per_launch;
+    float ms;                 /* fastest launch (CUDA events on the stream) */
+    int32_t sm_count;         /* cudaDevAttrMultiProcessorCount of the current device */
+    int32_t threads_per_sm;   /* resident threads per SM of the probe */
+    int32_t clock_mhz;        /* cudaDevAttrClockRate (the device's rated maximum), MHz */
+    int32_t reserved[4];
+} s3_peak_result;
+
+/*
+ * Measured FP32 (dt = S3_F32) or FP64 (S3_F64) FMA throughput of the current
+ * device: independent chains v = v * a + b in every thread of a grid that fills
+ * all SMs, timed with CUDA events on ``stream`` (one warm-up launch, then `reps`
+ * timed launches, 1..10000; the fastest is reported).  These are the peaks the
+ * ALU-bound series kernels are compared with; the paper has no counterpart of
+ * this entry point.  Synchronises ``stream``.  res: host.
+ */
+s3_status s3_fma_peak(s3_dtype dt, int32_t reps, s3_peak_result *res, void *stream);
 
 /* ------------------------------------------------------------- cleanup --- */
 

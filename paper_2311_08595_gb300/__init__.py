@@ -20,8 +20,9 @@ import ctypes
 import numpy as np
 
 from . import _lib
-from ._lib import (S3_DF64, S3_F32, S3_F64, S3_LAYOUT_CCSS, S3_LAYOUT_EDGE, S3_REDUCE_ATOMIC,  # noqa: F401
-                   S3_REDUCE_SEGMENTED, S3Error, check, load, ptr)
+from ._lib import (S3_DF64, S3_EINVAL, S3_ENOCONV, S3_ENOTSUP, S3_ERANGE, S3_F32, S3_F64,  # noqa: F401
+                   S3_LAYOUT_CCSS, S3_LAYOUT_EDGE, S3_REDUCE_ATOMIC, S3_REDUCE_SEGMENTED, S3Error, check, load,
+                   ptr)
 
 __all__ = [
     "Graph", "S3Error", "s3_options_init", "s3_format_inspect", "s3_build_format", "s3_graph_query",
@@ -30,7 +31,7 @@ __all__ = [
     "s3_nqz_options_init", "s3_sttsvc_f32_noalloc", "s3_destroy", "s3_version", "lib_path",
     "Batch", "s3_batch_options_init", "s3_batch_create", "s3_sttsvc_batched", "s3_batch_autotune",
     "s3_batch_destroy", "MLP", "s3_features", "s3_mlp_create", "s3_mlp_get_params", "s3_mlp_forward",
-    "s3_mlp_loss_grad", "s3_mlp_adam_step", "s3_warmstart", "s3_mlp_target", "s3_mlp_destroy",
+    "s3_mlp_loss_grad", "s3_mlp_adam_step", "s3_warmstart", "s3_mlp_target", "s3_mlp_destroy", "s3_fma_peak",
 ]
 
 
@@ -220,13 +221,27 @@ def s3_hcentrality(g, x0=None, x_out=None, stream=None, raise_on_noconv=True, **
 def s3_sttsvc_f32_noalloc(n, edge_ptr, members, x, y, rank, stream=None):
     """FP32 S^3TTVc that allocates no device memory (see include/s3ttvc.h).
 
-    edge_ptr (int64, m+1), members (int32), x and y (float32, n) are CUDA tensors
-    the caller already owns; the library uses only its fixed built-in scratch."""
-    for t, nm in ((edge_ptr, "edge_ptr"), (members, "members"), (x, "x"), (y, "y")):
+    edge_ptr (int64, m+1), members (int32), x and y (float32, at least n each) are
+    contiguous CUDA tensors on one device that the caller already owns; the
+    library uses only its fixed built-in scratch.  The call runs on the tensors'
+    device."""
+    import torch
+    n = int(n)
+    for t, nm, dt in ((edge_ptr, "edge_ptr", torch.int64), (members, "members", torch.int32),
+                      (x, "x", torch.float32), (y, "y", torch.float32)):
         if not t.is_cuda or not t.is_contiguous():
             raise ValueError(f"{nm} must be a contiguous CUDA tensor")
-    check(load().s3_sttsvc_f32_noalloc(int(n), edge_ptr.numel() - 1, int(rank), ptr(edge_ptr), ptr(members),
-                                       ptr(x), ptr(y), _stream(stream)))
+        if t.dtype != dt:
+            raise TypeError(f"{nm} must be {dt}")
+        if t.device != x.device:
+            raise ValueError(f"{nm} is on {t.device}, x on {x.device}: all tensors must share one device")
+    if edge_ptr.numel() < 1:
+        raise ValueError("edge_ptr needs m+1 >= 1 entries")
+    if x.numel() < n or y.numel() < n:
+        raise ValueError(f"x and y must hold at least n = {n} floats")
+    with torch.cuda.device(x.device):
+        check(load().s3_sttsvc_f32_noalloc(n, edge_ptr.numel() - 1, int(rank), ptr(edge_ptr), ptr(members),
+                                           ptr(x), ptr(y), _stream(stream)))
     return y
 
 
@@ -392,6 +407,14 @@ def s3_mlp_destroy(m):
     if m is not None and getattr(m, "handle", None):
         h, m.handle = m.handle, None
         check(load().s3_mlp_destroy(h))
+
+
+def s3_fma_peak(fp64=False, reps=20, stream=None):
+    """Measured FMA throughput of the current device (FP32, or FP64 with fp64=True)."""
+    r = _lib.s3_peak_result()
+    check(load().s3_fma_peak(S3_F64 if fp64 else S3_F32, int(reps), ctypes.byref(r), _stream(stream)))
+    return {"tflops": r.tflops, "ms": r.ms, "flops_per_launch": r.flops_per_launch, "sm_count": r.sm_count,
+            "threads_per_sm": r.threads_per_sm, "clock_mhz": r.clock_mhz}
 
 
 def s3_destroy(g):

@@ -17,7 +17,8 @@ LIB_PATH = os.path.join(HERE, "libs3ttvc.so")
 
 S3_MAX_RANK = 128
 S3_MLP_FEATURES, S3_MLP_HIDDEN, S3_MLP_PARAMS = 12, 64, 5057
-S3_OK, S3_EINVAL, S3_ENOMEM, S3_ECUDA, S3_ENOCONV, S3_ETIMEOUT, S3_ERANGE, S3_ENOTSUP = range(8)
+S3_OK, S3_EINVAL, S3_ENOMEM, S3_ECUDA, S3_ENOCONV = range(5)
+S3_ERANGE, S3_ENOTSUP = 6, 7
 S3_F32, S3_F64, S3_DF64 = 0, 1, 2
 S3_REDUCE_SEGMENTED, S3_REDUCE_ATOMIC = 0, 1
 S3_LAYOUT_EDGE, S3_LAYOUT_CCSS = 0, 1
@@ -35,7 +36,7 @@ class s3_options(ctypes.Structure):
                 ("build_ccss", ctypes.c_int32), ("device", ctypes.c_int32), ("thread_max_w", ctypes.c_int32),
                 ("block_threads", ctypes.c_int32), ("order", ctypes.c_int32), ("streams", ctypes.c_int32),
                 ("small_bucket_edges", ctypes.c_int32), ("closed_form_max_s", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 5)]
+                ("range_check", ctypes.c_int32), ("reserved", ctypes.c_int32 * 4)]
 
 
 class s3_format_info(ctypes.Structure):
@@ -82,6 +83,12 @@ class s3_tune_result(ctypes.Structure):
                 ("reserved", ctypes.c_int32), ("candidates", s3_tune_candidate * 32)]
 
 
+class s3_peak_result(ctypes.Structure):
+    _fields_ = [("tflops", ctypes.c_double), ("flops_per_launch", ctypes.c_double), ("ms", ctypes.c_float),
+                ("sm_count", ctypes.c_int32), ("threads_per_sm", ctypes.c_int32), ("clock_mhz", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 4)]
+
+
 _P = ctypes.c_void_p
 _I64 = ctypes.c_int64
 _I32 = ctypes.c_int32
@@ -116,6 +123,7 @@ SIGNATURES = {
     "s3_warmstart": (_I32, [_P, _P, _P, _P]),
     "s3_mlp_target": (_I32, [_P, _P, _P, _P]),
     "s3_mlp_destroy": (_I32, [_P]),
+    "s3_fma_peak": (_I32, [_I32, _I32, ctypes.POINTER(s3_peak_result), _P]),
     "s3_destroy": (_I32, [_P]),
     "s3_last_error": (ctypes.c_char_p, []),
     "s3_status_string": (ctypes.c_char_p, [_I32]),

@@ -29,6 +29,13 @@ s3_status cuda_fail(cudaError_t e, const char *what) {
     return fail(S3_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
 }
 
+s3_status mark_done(s3_graph_s *g, cudaStream_t st) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    S3_CUDA(cudaStreamIsCapturing(st, &cs));
+    if (cs == cudaStreamCaptureStatusNone) S3_CUDA(cudaEventRecord(g->ev_done, st));
+    return S3_OK;
+}
+
 s3_status prepare_device(int dev) {
     static std::mutex mu;
     static std::vector<char> done;
@@ -68,6 +75,18 @@ void free_all(s3_graph_s *g) {
     }
     if (g->ev_fork) cudaEventDestroy(g->ev_fork);
     g->ev_fork = nullptr;
+    if (g->ev_done) cudaEventDestroy(g->ev_done);
+    g->ev_done = nullptr;
+    if (g->qstream) cudaStreamDestroy(g->qstream);
+    g->qstream = nullptr;
+    if (g->h_range) cudaFreeHost(g->h_range);
+    g->h_range = nullptr;
+}
+
+// Wait for the handle's last call (its completion event), not for the whole device.
+s3_status wait_done(s3_graph_s *g) {
+    S3_CUDA(cudaEventSynchronize(g->ev_done));
+    return S3_OK;
 }
 
 }  // namespace
@@ -320,6 +339,7 @@ s3_status s3_build_format(int64_t n, int64_t m, const int64_t *edge_ptr, const i
     if (o.closed_form_max_s < -1 || o.closed_form_max_s > kClosedMaxS)
         return fail(S3_EINVAL, "closed_form_max_s must be in -1..6");
     if (o.order != S3_ORDER_DEGREE && o.order != S3_ORDER_INDEX) return fail(S3_EINVAL, "bad order");
+    if (o.range_check != 0 && o.range_check != 1) return fail(S3_EINVAL, "range_check must be 0 or 1");
     HostFormat f;
     try {
         s3_status st = build_host_format(n, m, edge_ptr, members, o, f);
@@ -403,6 +423,14 @@ s3_status s3_build_format(int64_t n, int64_t m, const int64_t *edge_ptr, const i
     if (f.has_ccss) {
         if ((st = upload_ccss(g, f)) != S3_OK) return bail(st);
     }
+    // completion event of the last call, query stream, pinned words of the range check
+    if (cudaEventCreateWithFlags(&g->ev_done, cudaEventDisableTiming) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&g->qstream, cudaStreamNonBlocking) != cudaSuccess)
+        return bail(cuda_fail(cudaGetLastError(), "cudaEventCreate"));
+    if (cudaHostAlloc((void **)&g->h_range, 2 * sizeof(unsigned long long), cudaHostAllocDefault) != cudaSuccess) {
+        g->h_range = nullptr;
+        return bail(cuda_fail(cudaGetLastError(), "cudaHostAlloc"));
+    }
     // concurrent size buckets: streams, events, and a cost estimate per bucket
     g->n_streams = o.streams > 0 ? std::min(o.streams, 8) : 4;
     if (g->n_streams > 1) {
@@ -480,6 +508,45 @@ s3_status s3_graph_query(s3_graph_t g, s3_format_info *info) {
     return S3_OK;
 }
 
+}  // extern "C"
+
+namespace s3 {
+namespace {
+
+// One S^3TTVc call on an already validated handle and arguments.
+s3_status sttsvc_dispatch(s3_graph_s *g, s3_dtype dt, int32_t layout, const void *x, void *y, cudaStream_t st) {
+    if (layout == S3_LAYOUT_EDGE) return run_edges(g, dt, x, y, 0, nullptr, st);
+    if (layout == S3_LAYOUT_CCSS) {
+        if (!g->has_ccss) return fail(S3_EINVAL, "handle was built without the CCSS forest");
+        return run_ccss(g, dt == S3_DF64 ? S3_F64 : dt, x, y, 0, nullptr, st);
+    }
+    return fail(S3_EINVAL, "bad layout");
+}
+
+// The call between two stream-ordered reads of the range counter; synchronises st and
+// returns S3_ERANGE when the counter moved (y is written either way).
+s3_status sttsvc_checked(s3_graph_s *g, s3_dtype dt, int32_t layout, const void *x, void *y, cudaStream_t st,
+                         void *y_host, size_t y_bytes) {
+    S3_CUDA(cudaMemcpyAsync(&g->h_range[0], g->d_range, sizeof(unsigned long long), cudaMemcpyDeviceToHost, st));
+    s3_status s = sttsvc_dispatch(g, dt, layout, x, y, st);
+    if (s != S3_OK) return s;
+    if (y_host) S3_CUDA(cudaMemcpyAsync(y_host, y, y_bytes, cudaMemcpyDeviceToHost, st));
+    S3_CUDA(cudaMemcpyAsync(&g->h_range[1], g->d_range, sizeof(unsigned long long), cudaMemcpyDeviceToHost, st));
+    s = mark_done(g, st);
+    if (s != S3_OK) return s;
+    S3_CUDA(cudaStreamSynchronize(st));
+    const unsigned long long d = g->h_range[1] - g->h_range[0];
+    if (d != 0)
+        return fail(S3_ERANGE, std::to_string(d) + " per-(edge, node) results of this call left the normal range of " +
+                                   (dt == S3_F32 ? "FP32" : "FP64"));
+    return S3_OK;
+}
+
+}  // namespace
+}  // namespace s3
+
+extern "C" {
+
 s3_status s3_sttsvc_layout(s3_graph_t g, s3_dtype dt, int32_t layout, const void *x, void *y, void *stream) {
     if (!g) return fail(S3_EINVAL, "graph is NULL");
     if (dt != S3_F32 && dt != S3_F64 && dt != S3_DF64) return fail(S3_EINVAL, "bad dtype");
@@ -489,12 +556,16 @@ s3_status s3_sttsvc_layout(s3_graph_t g, s3_dtype dt, int32_t layout, const void
     if (xb < yb + esz * g->n && yb < xb + esz * g->n) return fail(S3_EINVAL, "x and y overlap");
     DeviceGuard guard(g->device);
     cudaStream_t st = (cudaStream_t)stream;
-    if (layout == S3_LAYOUT_EDGE) return run_edges(g, dt, x, y, 0, nullptr, st);
-    if (layout == S3_LAYOUT_CCSS) {
-        if (!g->has_ccss) return fail(S3_EINVAL, "handle was built without the CCSS forest");
-        return run_ccss(g, dt == S3_DF64 ? S3_F64 : dt, x, y, 0, nullptr, st);
+    if (g->opt.range_check) {
+        cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+        S3_CUDA(cudaStreamIsCapturing(st, &cs));
+        if (cs != cudaStreamCaptureStatusNone)
+            return fail(S3_ENOTSUP, "range_check synchronises the stream: not allowed during stream capture");
+        return sttsvc_checked(g, dt, layout, x, y, st, nullptr, 0);
     }
-    return fail(S3_EINVAL, "bad layout");
+    s3_status s = sttsvc_dispatch(g, dt, layout, x, y, st);
+    if (s != S3_OK) return s;
+    return mark_done(g, st);
 }
 
 s3_status s3_sttsvc(s3_graph_t g, s3_dtype dt, const void *x, void *y, void *stream) {
@@ -510,11 +581,7 @@ s3_status s3_sttsvc_host(s3_graph_t g, s3_dtype dt, const void *x_host, void *y_
     cudaStream_t st = (cudaStream_t)stream;
     const size_t bytes = (dt == S3_F32 ? 4 : 8) * (size_t)g->n;
     S3_CUDA(cudaMemcpyAsync(g->d_xh, x_host, bytes, cudaMemcpyHostToDevice, st));
-    s3_status s = s3_sttsvc(g, dt, g->d_xh, g->d_yh, stream);
-    if (s != S3_OK) return s;
-    S3_CUDA(cudaMemcpyAsync(y_host, g->d_yh, bytes, cudaMemcpyDeviceToHost, st));
-    S3_CUDA(cudaStreamSynchronize(st));
-    return S3_OK;
+    return sttsvc_checked(g, dt, g->opt.layout, g->d_xh, g->d_yh, st, y_host, bytes);
 }
 
 s3_status s3_sttsvc_profile(s3_graph_t g, s3_dtype dt, const void *x, void *y, s3_profile *prof, void *stream) {
@@ -536,6 +603,8 @@ s3_status s3_sttsvc_profile(s3_graph_t g, s3_dtype dt, const void *x, void *y, s
     s3_status s = run_edges(g, dt, x, y, 0, nullptr, st, ev[1]);
     if (s != S3_OK) return s;
     S3_CUDA(cudaEventRecord(ev[2], st));
+    s = mark_done(g, st);
+    if (s != S3_OK) return s;
     S3_CUDA(cudaEventSynchronize(ev[2]));
     std::memset(prof, 0, sizeof(*prof));
     S3_CUDA(cudaEventElapsedTime(&prof->edge_ms, ev[0], ev[1]));
@@ -548,11 +617,13 @@ s3_status s3_sttsvc_profile(s3_graph_t g, s3_dtype dt, const void *x, void *y, s
 s3_status s3_range_events(s3_graph_t g, int64_t *count, int32_t reset) {
     if (!g || !count) return fail(S3_EINVAL, "NULL argument");
     DeviceGuard guard(g->device);
-    S3_CUDA(cudaDeviceSynchronize());
-    unsigned long long c = 0;
-    S3_CUDA(cudaMemcpy(&c, g->d_range, sizeof(c), cudaMemcpyDeviceToHost));
-    *count = (int64_t)c;
-    if (reset) S3_CUDA(cudaMemset(g->d_range, 0, sizeof(c)));
+    s3_status s = wait_done(g);
+    if (s != S3_OK) return s;
+    S3_CUDA(cudaMemcpyAsync(&g->h_range[0], g->d_range, sizeof(unsigned long long), cudaMemcpyDeviceToHost,
+                            g->qstream));
+    if (reset) S3_CUDA(cudaMemsetAsync(g->d_range, 0, sizeof(unsigned long long), g->qstream));
+    S3_CUDA(cudaStreamSynchronize(g->qstream));
+    *count = (int64_t)g->h_range[0];
     return S3_OK;
 }
 
@@ -571,9 +642,12 @@ s3_status s3_closed_form_query(s3_graph_t g, uint64_t *sizes_f32, uint64_t *size
         *rejected = 0;
         if (g->d_closed_count) {
             DeviceGuard guard(g->device);
-            S3_CUDA(cudaDeviceSynchronize());
+            s3_status s = wait_done(g);
+            if (s != S3_OK) return s;
             std::vector<int32_t> cnt(4 * g->buckets.size());
-            S3_CUDA(cudaMemcpy(cnt.data(), g->d_closed_count, sizeof(int32_t) * cnt.size(), cudaMemcpyDeviceToHost));
+            S3_CUDA(cudaMemcpyAsync(cnt.data(), g->d_closed_count, sizeof(int32_t) * cnt.size(), cudaMemcpyDeviceToHost,
+                                    g->qstream));
+            S3_CUDA(cudaStreamSynchronize(g->qstream));
             for (size_t k = 0; k < g->buckets.size(); ++k) {
                 unsigned long long t = 0;
                 std::memcpy(&t, &cnt[4 * k + 2], sizeof(t));
@@ -604,7 +678,6 @@ const char *s3_status_string(s3_status st) {
         case S3_ENOMEM: return "S3_ENOMEM";
         case S3_ECUDA: return "S3_ECUDA";
         case S3_ENOCONV: return "S3_ENOCONV";
-        case S3_ETIMEOUT: return "S3_ETIMEOUT";
         case S3_ERANGE: return "S3_ERANGE";
         case S3_ENOTSUP: return "S3_ENOTSUP";
     }

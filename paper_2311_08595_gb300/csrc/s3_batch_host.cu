@@ -373,7 +373,10 @@ s3_status s3_sttsvc_batched(s3_batch_t bt, s3_dtype dt, const void *const *x, vo
     // the shared-memory need depends on the element size
     s3_status s = ensure_tiles(bt, dt == S3_F32 ? 4 : 8);
     if (s != S3_OK) return s;
-    return run_batch(bt, dt, x, y, (cudaStream_t)stream);
+    s = run_batch(bt, dt, x, y, (cudaStream_t)stream);
+    if (s != S3_OK) return s;
+    // the batch writes the first graph's range counter: later queries on it wait for this call
+    return bt->graphs.empty() ? S3_OK : mark_done(bt->graphs[0], (cudaStream_t)stream);
 }
 
 s3_status s3_batch_autotune(s3_batch_t bt, s3_dtype dt, const void *const *x, void *const *y, s3_tune_result *res,

@@ -79,6 +79,12 @@ struct s3_graph_s {
     } nqz_exec[3];
 
     int32_t last_launches = 0;       // kernels launched by the last S^3TTVc call
+    // completion of the handle's last call (recorded on that call's stream unless the stream
+    // was being captured), the stream of the counter queries, and two pinned words that a
+    // range-checked call reads the range counter into (before, after)
+    cudaEvent_t ev_done = nullptr;
+    cudaStream_t qstream = nullptr;
+    unsigned long long *h_range = nullptr;
     uint32_t *d_feat_scratch = nullptr;  // warm-start feature counters (48 bytes per node)
     float *d_ws = nullptr;               // warm-start features, predictions, partials
     // concurrent buckets: forked streams and events, bucket order (heaviest first) and cost
@@ -143,6 +149,8 @@ struct DeviceGuard {
 
 s3_status cuda_fail(cudaError_t e, const char *what);
 s3_status prepare_device(int dev);
+// Record the completion of a call's work on st (skipped while st is being captured).
+s3_status mark_done(s3_graph_s *g, cudaStream_t st);
 // mid (optional) is recorded on st between the edge kernels and the reduce
 s3_status run_edges(s3_graph_s *g, s3_dtype dt, const void *x, void *y, int bias, const int32_t *skip,
                     cudaStream_t st, cudaEvent_t mid = nullptr);

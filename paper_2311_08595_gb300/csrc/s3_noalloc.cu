@@ -11,9 +11,9 @@
 // arrays plus x and y, and keeps its only scratch -- the FP32 two-sum
 // compensation term of every node -- in a fixed array that lives in this file
 // (`g_comp`, S3_NOALLOC_MAX_NODES floats).  The CUDA module holds that array
-// on every GPU that loads the library until the process exits.  The kernel is
-// the warp-per-edge series kernel of the handle-based path, reading members
-// from CSR and adding its results with atomics plus compensation.
+// on every GPU that loads the library until the process exits.  The kernel
+// runs the warp-per-edge series of the handle-based path on each edge's CSR
+// slice and adds its results with atomics plus compensation.
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -73,6 +73,8 @@ void fill_tables(int N, NoallocTables &t) {
 
 // One warp per edge over CSR input; results added to y with atomics and the
 // rounding error of each addition added to comp (both zeroed by the caller).
+// Edges of size >= 2 run the warp-per-edge series of the handle-based path
+// (warp_edge_compute) with the edge's CSR slice as a one-edge bucket.
 __global__ void __launch_bounds__(128) noalloc_edge_kernel(int64_t n, int64_t m, int32_t N,
                                                            const int64_t *__restrict__ edge_ptr,
                                                            const int32_t *__restrict__ members,
@@ -84,6 +86,10 @@ __global__ void __launch_bounds__(128) noalloc_edge_kernel(int64_t n, int64_t m,
     const int wib = threadIdx.x >> 5;
     const int wpb = blockDim.x >> 5;
     float *base = reinterpret_cast<float *>(smem_raw) + (int64_t)wib * per_warp;
+    EdgeOutArgs o{};
+    o.out = y;
+    o.comp = comp;
+    o.mode = kOutAtomicComp;
     for (int64_t e = (int64_t)blockIdx.x * wpb + wib; e < m; e += (int64_t)gridDim.x * wpb) {
         const int64_t e0 = edge_ptr[e];
         const int64_t len = edge_ptr[e + 1] - e0;
@@ -96,99 +102,31 @@ __global__ void __launch_bounds__(128) noalloc_edge_kernel(int64_t n, int64_t m,
             if (v < 0 || v >= n) ok = false;
         }
         if (!__all_sync(0xffffffffu, ok)) continue;
-        const int W = N - s + 1;
-        float *Xs = base;
-        float *C = Xs + s;
-        float *Pre = C + s;
-        float *Pc = Pre + (int64_t)(s > 2 ? s - 2 : 0) * W;
-        float *Q = Pc + W;
-        float *A = Q + W;
-        float *R = A + W;
-        float part = 0.f;
-        for (int i = lane; i < s; i += 32) {
-            float X = __ldg(x + __ldg(members + e0 + i));
-            Xs[i] = X;
-            part += fabsf(X);
-        }
-        const float S = warp_sum(part);
-        const int p = scale_exponent<float>(S, tab.target[s]);
-        const float g = Arith<float>::pow2(p);
         EdgeBucketArgs b{};
+        b.ids = members + e0;   // member i at ids[i * ld + 0]
+        b.m = 1;
+        b.ld = 1;
         b.s = s;
         b.N = N;
+        b.target = tab.target[s];
         b.K = tab.K[s];
         b.Km = tab.Km[s];
         b.Ke = tab.Ke[s];
-        __syncwarp();
-        for (int i = lane; i < s; i += 32) Xs[i] *= g;
-        __syncwarp();
-        if (s == 1) {
-            // c = x^(N-1): the series with an empty product
-            if (lane == 0) {
-                float X = Xs[0];
-                float r = 1.f;
-                for (int k = 1; k < N; ++k) r = r * (X / (float)k);  // X^(N-1)/(N-1)!
-                C[0] = r;
-            }
-        } else {
-            power_table_warp<float>(Xs[0], Pc, W);
-            __syncwarp();
-            for (int i = 1; i <= s - 2; ++i) {
-                float *slotp = Pre + (int64_t)(i - 1) * W;
-                for (int j = lane; j < W; j += 32) slotp[j] = Pc[j];
-                power_table_warp<float>(Xs[i], A, W);
-                __syncwarp();
-                for (int j = lane; j < W; j += 32) {
-                    float acc = 0.f;
-                    for (int jp = 0; jp <= j; ++jp) acc = fmaf(A[j - jp], slotp[jp], acc);
-                    Pc[j] = acc;
-                }
-                __syncwarp();
-            }
-            power_table_warp<float>(Xs[s - 1], Q, W);
-            __syncwarp();
-            float fp = 0.f;
-            for (int j = lane; j <= W - 2; j += 32) fp = fmaf(Pc[j], Q[W - 2 - j], fp);
-            const float F = warp_sum(fp);
-            if (lane == 0) C[s - 1] = F + Pc[W - 1];
-            float top = 0.f;
-            for (int q = s - 2; q >= 1; --q) {
-                const float *pre = Pre + (int64_t)(q - 1) * W;
-                float dp = 0.f;
-                for (int j = lane; j < W; j += 32) dp = fmaf(pre[j], Q[W - 1 - j], dp);
-                float D = warp_sum(dp);
-                if (lane == 0) C[q] = F + D;
-                power_table_warp<float>(Xs[q], A, W);
-                __syncwarp();
-                if (q >= 2) {
-                    for (int j = lane; j < W; j += 32) {
-                        float acc = 0.f;
-                        for (int jp = 0; jp <= j; ++jp) acc = fmaf(A[j - jp], Q[jp], acc);
-                        R[j] = acc;
-                    }
-                    __syncwarp();
-                    float *t = Q;
-                    Q = R;
-                    R = t;
-                } else {
-                    float tp = 0.f;
-                    for (int jp = lane; jp < W; jp += 32) tp = fmaf(A[W - 1 - jp], Q[jp], tp);
-                    top = warp_sum(tp);
-                }
-            }
-            if (lane == 0) C[0] = F + (s == 2 ? Q[W - 1] : top);
+        if (s >= 2) {
+            warp_edge_compute<float>(b, x, o, 0, N - s + 1, base);
+            continue;
         }
-        __syncwarp();
-        for (int q = lane; q < s; q += 32) {
-            float c;
-            if (s == 1) {
-                // undo the scaling: (g x)^(N-1)/(N-1)! * K(1,N) g^-(N-1)
-                c = finalize_value<float>(C[0], b, p, 0, nullptr);
-            } else {
-                c = finalize_value<float>(C[q], b, p, 0, nullptr);
-            }
-            int v = __ldg(members + e0 + q);
-            float old = atomicAdd(y + v, c);
+        // size 1: c = K(1,N) [t^(N-1)] e^(x t) = x^(N-1), the series with an empty product,
+        // formed as (g x)^(N-1)/(N-1)! and scaled back by K(1,N) g^-(N-1)
+        if (lane == 0) {
+            const int v = __ldg(members + e0);
+            const float X = __ldg(x + v);
+            const int p = scale_exponent<float>(fabsf(X), b.target);
+            const float gx = X * Arith<float>::pow2(p);
+            float r = 1.f;
+            for (int k = 1; k < N; ++k) r = r * (gx / (float)k);
+            const float c = finalize_value<float>(r, b, p, 0, nullptr);
+            const float old = atomicAdd(y + v, c);
             float sm, er;
             two_sum(old, c, sm, er);
             if (er != 0.f) atomicAdd(comp + v, er);

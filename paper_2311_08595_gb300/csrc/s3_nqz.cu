@@ -422,6 +422,10 @@ s3_status s3_hcentrality(s3_graph_t g, const s3_nqz_options *opt_in, const doubl
         res->converged = (res->lambda_max - res->lambda_min) / res->lambda_min < opt.tol;
     }
     S3_CUDA(cudaMemcpyAsync(x_out, b.x64, sizeof(double) * n, cudaMemcpyDeviceToDevice, st));
+    {
+        s3_status ms = mark_done(g, st);
+        if (ms != S3_OK) return ms;
+    }
     S3_CUDA(cudaStreamSynchronize(st));
     res->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
     if (flags[F_RANGE] && !res->converged) return fail(S3_ERANGE, "ratio z/x^(N-1) left the FP64 range");

@@ -30,7 +30,7 @@ __all__ = [
     "uniform_members", "chung_lu_members", "largest_component",
     "random_uniform_hypergraph", "config_small", "config_powerlaw",
     "config_large_rank", "config_batched", "tiny_case", "fig1_example",
-    "sunflower", "nested", "paper_s_family", "x_uniform", "x_constant",
+    "sunflower", "nested", "paper_s_family", "x_uniform", "x_constant", "x_degree_like",
 ]
 
 
@@ -313,3 +313,13 @@ def x_uniform(n, lo, hi, seed, dtype=np.float64):
 
 def x_constant(n, value, dtype=np.float64):
     return np.full(n, value, dtype=dtype)
+
+
+def x_degree_like(hg, seed=5):
+    """A positive vector shaped like a centrality: degree^(1/(N-1)) of each node (degree
+    0 counts as 1), times a U(0.9, 1.1) jitter, rescaled to maximum 1.  This is the x of
+    the power-law benchmark workload."""
+    rng = np.random.default_rng(seed)
+    d = np.maximum(hg.degrees(), 1).astype(np.float64)
+    x = d ** (1.0 / (hg.rank - 1)) * rng.uniform(0.9, 1.1, hg.n)
+    return x / x.max()
