@@ -49,7 +49,7 @@ def measured_peaks():
     return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
 
 
-def algorithmic_counts(edges_per_size, N, closed_sizes=()):
+def algorithmic_counts(edges_per_size, N, closed_sizes=(), bern_sizes=()):
     """FLOPs of one FP32 S^3TTVc call by the edge-layout algorithm.
 
     Per edge of size s >= 2 with window W = N - s + 1 (series):
@@ -57,6 +57,7 @@ def algorithmic_counts(edges_per_size, N, closed_sizes=()):
                          (s >= 3), plus W FMAs for the last suffix coefficient;
       dots: (W-1) for [t^(N-1)] F_e and W for each of the s-2 interior nodes;
       power tables: 2(s-1) tables of W coefficients, 2 multiplies per coefficient.
+    Sizes in bern_sizes count as bernoulli_flops gives them.
     Per edge of a size in closed_sizes (inclusion-exclusion): for each of the 2^s - 1
     subsets one add (its sum), floor(log2 n) + popcount(n) - 1 multiplies (sum^n,
     n = N-1) and one add (the sum of |terms|), then s 2^(s-1) signed adds.  The
@@ -75,6 +76,9 @@ def algorithmic_counts(edges_per_size, N, closed_sizes=()):
         if s in closed_sizes:
             mul += cnt * ((2 ** s - 1) * (2 + n.bit_length() - 1 + bin(n).count("1") - 1) + s * 2 ** (s - 1))
             continue
+        if s in bern_sizes:
+            mul += bernoulli_flops(edges_per_size, N, [s])
+            continue
         W = N - s + 1
         f = (W - 1) + max(s - 2, 0) * W
         if s >= 3:
@@ -82,6 +86,26 @@ def algorithmic_counts(edges_per_size, N, closed_sizes=()):
         fma += cnt * f
         mul += cnt * 2 * (s - 1) * 2 * W
     return 2 * fma + mul, fma
+
+
+def bernoulli_flops(edges_per_size, N, sizes):
+    """FLOPs of the Bernoulli-form launch (csrc/s3_bern.cuh) for the edge sizes it takes.
+
+    Per edge of size s, window W = N - s + 1: the first member's series g (2(W-1)
+    multiplies), then per further member the ratios x/(k+1) (W-1 multiplies), the
+    truncated product (W(W-1)/2 multiply-adds) and the running product (1 multiply);
+    the coefficients H_k = G[W-1-k] beta_k (W multiplies); per member the sum in
+    x^4-Horner form (2 + 2 ceil((W-2)/4) + 2 ceil((W-4)/4) + 4 flops with x^2, x^4 and
+    the two leading terms), the gate (3) and P / x_i times the sum (2).  One
+    multiply-add = 2 flops."""
+    total = 0
+    for s in sizes:
+        cnt = edges_per_size[s]
+        W = N - s + 1
+        per = 2 * (W - 1) + (s - 1) * ((W - 1) + W * (W - 1) + 1) + W
+        per += s * (4 + 2 * -(-max(W - 2, 0) // 4) + 2 * -(-max(W - 4, 0) // 4) + 2 + 3 + 2)
+        total += cnt * per
+    return total
 
 
 def hbm_bytes(nnz, n, esz=4, deterministic=True, comp=False):
@@ -184,13 +208,21 @@ def make_workload(n=None):
 
 # ------------------------------------------------------------ CPU oracle ---
 
+def host_cores():
+    """Host threads this process may run on (its CPU affinity): the oracle is timed on all of them."""
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
 def time_oracle(hg, x, budget_s=12.0, seed=0):
     """Time the FP64 CPU oracle (Algorithm 2) on a bounded random node sample.
 
     Returns (members/s, cores, sample description).  A 'member' is one
     (edge, node) contribution, the unit of the GPU metric."""
     import oracle
-    cores = oracle.max_threads()
+    cores = host_cores()
     deg = hg.degrees()
     rng = np.random.default_rng(seed)
     perm = rng.permutation(hg.n)
@@ -218,7 +250,7 @@ def run_reference(args):
         return 0
     hg, x = make_workload()
     import oracle
-    cores = oracle.max_threads()
+    cores = host_cores()
     deg = hg.degrees()
     rng = np.random.default_rng(1)
     nodes = rng.permutation(hg.n)[:20000]
@@ -293,8 +325,11 @@ def run_gpu(args):
     prof = [s3.s3_sttsvc_profile(g, x, y) for _ in range(20)]
     edge_ms = float(np.mean([p["edge_ms"] for p in prof]))
     reduce_ms = float(np.mean([p["reduce_ms"] for p in prof]))
+    bern_ms = float(np.mean([p["bern_ms"] for p in prof]))
     closed = s3.s3_closed_form_query(g)
-    flops, fmas = algorithmic_counts(info["edges_per_size"], N, closed["f32"])
+    bern = s3.s3_bernoulli_query(g)
+    flops, fmas = algorithmic_counts(info["edges_per_size"], N, closed["f32"], bern["f32"])
+    bflops = bernoulli_flops(info["edges_per_size"], N, bern["f32"])
     peaks, peak_kind = measured_peaks()
     clocks = clk.summary()
     # measured FMA peaks of this device (FP32, FP64), clocks sampled while they run
@@ -324,14 +359,23 @@ def run_gpu(args):
                        l2="inputs larger than L2: ids+slots+buffer = 16 bytes x members" if nnz > 8_000_000
                        else "inputs smaller than L2 (reduced workload)",
                        nnz=nnz, parallelism=f"replicas x{ws}"),
-        "roofline": {"bound": "alu", "kernel": "per-edge kernels of one call: series products for all sizes but "
-                     + ",".join(map(str, closed["f32"])) + ", closed form for those",
-                     "achieved": achieved_tflops, "peak": p32["tflops"], "unit": "TFLOP/s",
-                     "frac": achieved_tflops / p32["tflops"], "traffic": traffic,
+        "roofline": {"bound": "alu", "kernel": "edge_bern_kernel<float> (one launch per call: edge sizes "
+                     + f"{min(bern['f32'])}-{max(bern['f32'])}, the Bernoulli form)" if bern["f32"] else "none",
+                     "achieved": bflops / (bern_ms * 1e-3) / 1e12 if bern_ms > 0 else None,
+                     "peak": p32["tflops"], "unit": "TFLOP/s",
+                     "frac": bflops / (bern_ms * 1e-3) / 1e12 / p32["tflops"] if bern_ms > 0 else None,
+                     "traffic": traffic,
                      "peak_note": "of measured: FP32 FMA-chain probe (s3_fma_peak) on this device, "
                                   f"{p32['sm_count']} SMs, median SM clock {pclocks['sm_mhz']} MHz during the probe",
-                     "algorithmic_flops_per_call": flops, "edge_ms": edge_ms, "reduce_ms": reduce_ms,
-                     "edge_ms_x_sm_mhz": edge_ms * (clocks["sm_mhz"] or 0.0)},
+                     "algorithmic_flops_per_launch": bflops, "launch_ms": bern_ms,
+                     "launch_ms_note": "CUDA events around the launch on the stream it runs on, mean of 20 calls"},
+        "edge_phase": {"bound": "alu", "kernels": "all per-edge kernels of one call (closed form for sizes "
+                       + ",".join(map(str, closed["f32"])) + ", Bernoulli form for "
+                       + (f"{min(bern['f32'])}-{max(bern['f32'])}" if bern["f32"] else "none") + ", series otherwise)",
+                       "achieved": achieved_tflops, "peak": p32["tflops"], "unit": "TFLOP/s",
+                       "frac": achieved_tflops / p32["tflops"], "algorithmic_flops_per_call": flops,
+                       "edge_ms": edge_ms, "reduce_ms": reduce_ms,
+                       "edge_ms_x_sm_mhz": edge_ms * (clocks["sm_mhz"] or 0.0)},
         "hbm": {"algorithmic_bytes_per_call": bytes_call, "achieved_gbs": bytes_call / (ms * 1e-3) / 1e9,
                 "peak_gbs": peaks["hbm_gbs"], "frac": bytes_call / (ms * 1e-3) / 1e9 / peaks["hbm_gbs"],
                 "peak_kind": peak_kind, "layout_bytes_per_call": layout_bytes(nnz, n),
@@ -380,6 +424,7 @@ def run_gpu(args):
     if rank == 0 and ws == 1 and not args.skip_extras:
         out["large_rank"] = large_rank(dev)
         out["layouts"] = layouts(dev)
+        out["cpu_comparators"] = cpu_comparators(dev)
         out["centrality"] = centrality(hg, dev)
         rate, cores, sample = time_oracle(hg, x_np)
         out["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample}
@@ -445,26 +490,37 @@ def batched(dev, scale=1.0, nvec=16, reps=3):
             "max_rel_diff_vs_single": err, "build_s": t_build}
 
 
+WARM_WEIGHTS = os.path.join(ROOT, "paper_2311_08595_gb300", "data", "warmstart_500x50k.npy")
+
+
 def warm_start(lcc, dev, graphs=48, n=50000, epochs=20):
-    """Learned warm start: trained on `graphs` power-law hypergraphs of n nodes (m = 5n, same
-    recipe as the workload), evaluated on the workload's largest component: NQZ to 1e-8 from the
-    uniform start vs from the network's prediction (features + MLP time included)."""
+    """Learned warm start on the workload's largest component: NQZ to 1e-8 from the uniform start
+    vs from the network's prediction (features + MLP time included).  The network is the one the
+    package ships (trained by `python -m paper_2311_08595_gb300.warmstart --graphs 500 --n 50000`
+    on 500 power-law hypergraphs of n = 50k, the recipe of the workload); without that file it is
+    trained here on `graphs` such hypergraphs."""
     import s3synth
+    from paper_2311_08595_gb300 import s3_mlp_create
     from paper_2311_08595_gb300 import warmstart as ws
-    rng = np.random.default_rng(2024)
-    t0 = time.perf_counter()
-    hgs = [s3synth.largest_component(s3synth.config_powerlaw(n=n, m=5 * n, seed=int(rng.integers(1 << 30))))[0]
-           for _ in range(graphs)]
-    feat, tgt = ws.build_dataset(hgs)
-    t_data = time.perf_counter() - t0
-    t0 = time.perf_counter()
-    model, hist = ws.train(feat, tgt, epochs=epochs, batch=65536, lr=2e-3)
-    t_train = time.perf_counter() - t0
     out = {}
+    if os.path.exists(WARM_WEIGHTS):
+        model = s3_mlp_create(params=np.load(WARM_WEIGHTS))
+        out["weights"] = "shipped: 500 training hypergraphs of n = 50k (warmstart.py)"
+    else:
+        rng = np.random.default_rng(2024)
+        t0 = time.perf_counter()
+        hgs = [s3synth.largest_component(s3synth.config_powerlaw(n=n, m=5 * n, seed=int(rng.integers(1 << 30))))[0]
+               for _ in range(graphs)]
+        feat, tgt = ws.build_dataset(hgs)
+        t_data = time.perf_counter() - t0
+        t0 = time.perf_counter()
+        model, hist = ws.train(feat, tgt, epochs=epochs, batch=65536, lr=2e-3)
+        out.update({"weights": f"trained here: {graphs} hypergraphs of n = {n}", "train_nodes": int(feat.shape[0]),
+                    "epochs": epochs, "loss_first": hist[0][1], "loss_last": hist[-1][1], "data_s": t_data,
+                    "train_s": time.perf_counter() - t0})
     for name, prec in (("fp64", 0), ("fp32_mixed", 1), ("fp32_then_double_float", 2), ("double_float", 3)):
         out[name] = ws.evaluate(lcc, model, tol=1e-8, precision=prec)
-    out.update({"train_graphs": graphs, "train_n": n, "train_nodes": int(feat.shape[0]), "epochs": epochs,
-                "loss_first": hist[0][1], "loss_last": hist[-1][1], "data_s": t_data, "train_s": t_train})
+    out["start_cost"] = ws.start_cost(lcc, model)
     return out
 
 
@@ -533,7 +589,7 @@ def large_rank(dev, sample=300):
     d = hg.degrees()
     rel = np.abs(a - b)[d > 0] / np.abs(b)[d > 0]
     nodes = np.random.default_rng(0).choice(np.nonzero(d > 0)[0], size=sample, replace=False)
-    want = oracle.ttsv1(hg, x_np, nodes=nodes, nthreads=oracle.max_threads())
+    want = oracle.ttsv1(hg, x_np, nodes=nodes, nthreads=host_cores())
     e64 = float(np.max(np.abs(b[nodes] - want) / np.abs(want)))
     s3.s3_destroy(g)
     return {"workload": "largerank n=200k m=1M geometric(0.1) sizes on 2..100, x~U(0.5,1.5)", "nnz": hg.nnz,
@@ -577,6 +633,71 @@ def layouts(dev):
                      "ccss_products": info["ccss_products"], "edge_layout_products": edge_products,
                      "max_rel_diff": diff}
         s3.s3_destroy(g)
+    return out
+
+
+def cpu_comparators(dev, budget_s=8.0):
+    """The paper's own CPU algorithms (Algorithm 4, memoised DFS on the CCSS forest; Algorithm 3,
+    its naive leaf-to-root baseline) in FP64 on all host cores, next to the GPU library on the
+    same hypergraphs: the power-law recipe at n=200k, m=1M (rank 25), the sunflower and nested
+    structures of Fig. 3, and the Table I style rank family (sizes 5, 10, .., r).  Each CPU
+    algorithm runs on a bounded sample of whole trees (roots) of the forest, grown until one
+    run takes about budget_s / 4; members/s counts the special leaves (edge, node) processed."""
+    import torch
+
+    import baseline
+    import paper_2311_08595_gb300 as s3
+    import s3synth
+    cores = host_cores()
+    cases = {"powerlaw_n200k_m1M_r25": s3synth.config_powerlaw(n=200000, m=1000000, rank=25, seed=9),
+             "nested_4000x6": s3synth.nested(chains=4000, length=6, start=5, step=5, n=200000),
+             "sunflower_20000x12_core8": s3synth.sunflower(petals=20000, k=12, core=8, n=100000)}
+    for r in (15, 25, 35):
+        cases[f"s_family_r{r}"] = s3synth.paper_s_family(r, n=100000, m=100000, seed=r)
+    out = {"cores": cores}
+    for name, hg in cases.items():
+        x = s3synth.x_uniform(hg.n, 0.5, 1.5, 17)
+        t0 = time.perf_counter()
+        f = baseline.Forest(hg)
+        t_build = time.perf_counter() - t0
+        res = {"n": hg.n, "m": hg.m, "nnz": hg.nnz, "rank": hg.rank, "forest_nodes": f.nodes,
+               "products_alg3": f.products3, "products_alg4": f.products4, "forest_build_s": t_build}
+        for alg in ("alg4", "alg3"):
+            run = getattr(f, alg)
+            k = max(1, f.roots // 256)
+            while True:
+                t0 = time.perf_counter()
+                run(x, nthreads=cores, roots=(0, k))
+                dt = time.perf_counter() - t0
+                if dt >= budget_s / 4 or k >= f.roots:
+                    break
+                k = min(f.roots, k * 4)
+            leaves = f.leaves_in_roots(0, k)
+            res[alg] = {"members_per_s": leaves / dt, "sample": f"{k} of {f.roots} trees, {leaves} members",
+                        "seconds": dt}
+        g = s3.s3_build_format(hg.n, hg.edge_ptr, hg.members, build_ccss=1)
+        for dt_name, dt in (("fp64", torch.float64), ("fp32", torch.float32)):
+            xd = torch.tensor(x, dtype=dt, device=dev)
+            yd = torch.empty_like(xd)
+            ms = _time_calls(g, xd, yd, 20)
+            res[f"gpu_{dt_name}_members_per_s"] = hg.nnz / (ms * 1e-3)
+        xd = torch.tensor(x, dtype=torch.float64, device=dev)
+        yc = torch.empty_like(xd)
+        s3.s3_sttsvc_layout(g, s3.S3_LAYOUT_CCSS, xd, yc)
+        torch.cuda.synchronize()
+        st = torch.cuda.current_stream()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        for _ in range(5):
+            s3.s3_sttsvc_layout(g, s3.S3_LAYOUT_CCSS, xd, yc)
+        e1.record(st)
+        torch.cuda.synchronize()
+        res["gpu_ccss_fp64_members_per_s"] = hg.nnz / (e0.elapsed_time(e1) / 5 * 1e-3)
+        res["gpu_fp64_vs_alg4"] = res["gpu_fp64_members_per_s"] / res["alg4"]["members_per_s"]
+        res["alg4_vs_alg3"] = res["alg4"]["members_per_s"] / res["alg3"]["members_per_s"]
+        s3.s3_destroy(g)
+        del f
+        out[name] = res
     return out
 
 

@@ -125,7 +125,17 @@ typedef struct {
                               written).  Not allowed while the stream is being captured into a
                               CUDA graph (S3_ENOTSUP).  0 = default: asynchronous, such results
                               are only counted */
-    int32_t reserved[4];
+    int32_t bernoulli;     /* FP32/FP64 buckets of edges of size 6..64 whose window N-|e|+1 is at most
+                              thread_max_w and that do not use the closed form are evaluated in one
+                              launch by the Bernoulli form of the leave-one-out: the product G of the
+                              series (e^(x_u t) - 1)/(x_u t) over the whole edge, then for each member
+                              v the sum over k of G's coefficients times B_k x_v^k / k! (Bernoulli
+                              numbers; E(x_v)/Ebar(x_v) = 1/(1 - e^(-x_v t)), Sec. II-A), where it
+                              costs fewer operations than the prefix/suffix products.  Edges whose
+                              alternating sum would amplify rounding errors more than 4x (FP32) or
+                              64x (FP64), or that hold x < 0, are recomputed with the series.
+                              0 = default (on), -1 = never */
+    int32_t reserved[3];
 } s3_options;
 
 typedef enum { S3_ORDER_DEGREE = 0, S3_ORDER_INDEX = 1 } s3_order;
@@ -212,14 +222,16 @@ typedef struct {
     float reduce_ms;   /* segmented reduce, or the compensation pass of the atomic mode */
     float total_ms;
     int32_t launches;  /* kernels launched by the call */
-    int32_t reserved[4];
+    float bern_ms;     /* the Bernoulli-form launch alone (events on its own stream); 0 if none */
+    int32_t reserved[3];
 } s3_profile;
 
 /*
  * Run s3_sttsvc once (edge layout) with CUDA events recorded on ``stream``
  * before the edge kernels, between them and the reduce, and after the
- * reduce; synchronises ``stream`` and writes the elapsed times to *prof
- * (host).  Arguments as s3_sttsvc.
+ * reduce, and around the Bernoulli-form launch on the stream it runs on;
+ * synchronises ``stream`` and writes the elapsed times to *prof (host).
+ * Arguments as s3_sttsvc.
  */
 s3_status s3_sttsvc_profile(s3_graph_t g, s3_dtype dt, const void *x, void *y, s3_profile *prof, void *stream);
 
@@ -241,6 +253,16 @@ s3_status s3_range_events(s3_graph_t g, int64_t *count, int32_t reset);
  * host.
  */
 s3_status s3_closed_form_query(s3_graph_t g, uint64_t *sizes_f32, uint64_t *sizes_f64, int64_t *rejected);
+
+/*
+ * Bernoulli-form evaluation (s3_options.bernoulli) on this handle:
+ * *sizes_f32 / *sizes_f64 = bit mask of the edge sizes s (bit s-1, s <= 64)
+ * whose bucket uses it for FP32 / FP64 calls; *rejected = edges that failed
+ * its amplification gate and were recomputed with the series, summed over all
+ * calls since the handle was built (waits for the handle's last call only).
+ * Any pointer may be NULL.  All host.
+ */
+s3_status s3_bernoulli_query(s3_graph_t g, uint64_t *sizes_f32, uint64_t *sizes_f64, int64_t *rejected);
 
 /* ------------------------------------------------------------------ NQZ --- */
 
@@ -282,6 +304,69 @@ s3_status s3_nqz_options_init(s3_nqz_options *opt);
  */
 s3_status s3_hcentrality(s3_graph_t g, const s3_nqz_options *opt, const double *x0, double *x_out,
                          s3_nqz_result *res, void *stream);
+
+/* ------------------------------------- Z-eigenpairs and symmetric CP --- */
+
+typedef struct {
+    double alpha;          /* shift (>= 0); 0 = plain higher-order power method */
+    double tol;            /* stop when |lambda_k - lambda_(k-1)| < tol max(1, |lambda_k|); default 1e-12 */
+    int32_t max_iter;      /* <= 0 = 10000 */
+    int32_t reserved[7];
+} s3_zeig_options;
+
+typedef struct {
+    double lambda;         /* x . B x^(N-1) at the returned x */
+    int32_t iters;         /* normalisation steps taken */
+    int32_t converged;
+    double seconds;
+    int32_t reserved[4];
+} s3_zeig_result;
+
+s3_status s3_zeig_options_init(s3_zeig_options *opt);
+
+/*
+ * A Z-eigenpair B x^(N-1) = lambda x, ||x||_2 = 1, of the blowup tensor by the
+ * shifted symmetric higher-order power method (the shifted-power method the
+ * paper names as a consumer of S^3TTVc, Sec. I):
+ *     x <- (B x^(N-1) + alpha x) / ||B x^(N-1) + alpha x||_2.
+ * Each step is one FP64 S^3TTVc (on x / max|x|, so any rank stays in range)
+ * and FP64 vector kernels; the host checks lambda after each step.
+ * x0: device, n doubles (any nonzero start; NULL = the uniform unit vector).
+ * x_out: device, n doubles, written.  res: host.  Synchronous on ``stream``;
+ * S3_ENOCONV (x_out, res written) if max_iter steps do not reach tol,
+ * S3_ERANGE if lambda leaves the FP64 range.
+ */
+s3_status s3_zeigenpair(s3_graph_t g, const s3_zeig_options *opt, const double *x0, double *x_out,
+                        s3_zeig_result *res, void *stream);
+
+/*
+ * Greedy rank-R symmetric CP approximation B ~ sum_r lambda_r x_r^(outer N)
+ * (the paper names symmetric CP decomposition as a consumer of S^3TTVc, Sec. I):
+ * component r is the s3_zeigenpair of B - sum_{q<r} lambda_q x_q^(outer N),
+ * whose product with x^(N-1) is B x^(N-1) - sum_q lambda_q (x_q . x)^(N-1) x_q.
+ * R: 1..32.  X0: device, R rows of n doubles (start of each component) or NULL
+ * (uniform starts).  X: device, R rows of n doubles, written (unit vectors).
+ * lambdas: host, R doubles, written.  iters: host, R ints, or NULL.
+ * Synchronous on ``stream``; S3_ENOCONV if some component did not converge.
+ */
+s3_status s3_symmetric_cp(s3_graph_t g, int32_t R, const s3_zeig_options *opt, const double *X0, double *X,
+                          double *lambdas, int32_t *iters, void *stream);
+
+/*
+ * One update of Algorithm 1 from a complete z = B xhat^(N-1) that the caller
+ * assembled -- e.g. the sum over GPUs of the partial results of handles built
+ * on disjoint edge sets of one hypergraph (edge-sharded S^3TTVc, FP64):
+ * lambda[0], lambda[1] = min and max over v of z_v / xhat_v^(N-1) (the bracket
+ * of this iterate; it does not depend on the scale of xhat), and the next
+ * iterate r = z^[1/(N-1)] written twice: x_next with 1-norm 1 (Algorithm 1's
+ * x) and xhat_next = r / max(r) (max 1: the input of the next S^3TTVc, which
+ * keeps z in range).  FP64 throughout.  z, xhat, x_next, xhat_next: device,
+ * n doubles (x_next and xhat_next distinct; either may alias xhat).  lambda:
+ * host, 2 doubles.  Synchronous on ``stream``; S3_ERANGE if a ratio or a root
+ * leaves the FP64 range (a node in no edge, or x_v = 0).
+ */
+s3_status s3_nqz_update(s3_graph_t g, const double *z, const double *xhat, double *x_next, double *xhat_next,
+                        double *lambda, void *stream);
 
 /* -------------------------------------------------------------- batches --- */
 

@@ -27,8 +27,10 @@ from ._lib import (S3_DF64, S3_EINVAL, S3_ENOCONV, S3_ENOTSUP, S3_ERANGE, S3_F32
 __all__ = [
     "Graph", "S3Error", "s3_options_init", "s3_format_inspect", "s3_build_format", "s3_graph_query",
     "s3_sttsvc", "s3_sttsvc_layout", "s3_sttsvc_host", "s3_sttsvc_profile", "s3_range_events", "s3_closed_form_query",
+    "s3_bernoulli_query",
     "s3_hcentrality",
     "s3_nqz_options_init", "s3_sttsvc_f32_noalloc", "s3_destroy", "s3_version", "lib_path",
+    "s3_zeig_options_init", "s3_zeigenpair", "s3_symmetric_cp", "s3_nqz_update",
     "Batch", "s3_batch_options_init", "s3_batch_create", "s3_sttsvc_batched", "s3_batch_autotune",
     "s3_batch_destroy", "MLP", "s3_features", "s3_mlp_create", "s3_mlp_get_params", "s3_mlp_forward",
     "s3_mlp_loss_grad", "s3_mlp_adam_step", "s3_warmstart", "s3_mlp_target", "s3_mlp_destroy", "s3_fma_peak",
@@ -170,7 +172,7 @@ def s3_sttsvc_profile(g, x, y, stream=None, df=False):
     check(load().s3_sttsvc_profile(g.handle, _dtype_code(x, df), ptr(x), ptr(y), ctypes.byref(prof),
                                    _stream(stream)))
     return {"edge_ms": prof.edge_ms, "reduce_ms": prof.reduce_ms, "total_ms": prof.total_ms,
-            "launches": prof.launches}
+            "launches": prof.launches, "bern_ms": prof.bern_ms}
 
 
 def s3_range_events(g, reset=False):
@@ -185,6 +187,15 @@ def s3_closed_form_query(g):
     a, b, r = ctypes.c_uint64(), ctypes.c_uint64(), ctypes.c_int64()
     check(load().s3_closed_form_query(g.handle, ctypes.byref(a), ctypes.byref(b), ctypes.byref(r)))
     sizes = lambda m: [s for s in range(64) if (m >> s) & 1]
+    return {"f32": sizes(a.value), "f64": sizes(b.value), "rejected": int(r.value)}
+
+
+def s3_bernoulli_query(g):
+    """Edge sizes evaluated in the Bernoulli form for FP32 and for FP64 calls, and the edges its
+    gate sent back to the series so far: {"f32": [s, ...], "f64": [...], "rejected": k}."""
+    a, b, r = ctypes.c_uint64(), ctypes.c_uint64(), ctypes.c_int64()
+    check(load().s3_bernoulli_query(g.handle, ctypes.byref(a), ctypes.byref(b), ctypes.byref(r)))
+    sizes = lambda m: [s + 1 for s in range(64) if (m >> s) & 1]
     return {"f32": sizes(a.value), "f64": sizes(b.value), "rejected": int(r.value)}
 
 
@@ -216,6 +227,62 @@ def s3_hcentrality(g, x0=None, x_out=None, stream=None, raise_on_noconv=True, **
     if st != _lib.S3_OK and not (st == _lib.S3_ENOCONV and not raise_on_noconv):
         check(st)
     return x_out, out
+
+
+def s3_nqz_update(g, z, xhat, x_next, xhat_next, stream=None):
+    """One Algorithm 1 update from a complete z (float64 CUDA tensors): returns (lambda_min, lambda_max)
+    and writes the next iterate to x_next (1-norm 1) and xhat_next (max 1)."""
+    for t, nm in ((z, "z"), (xhat, "xhat"), (x_next, "x_next"), (xhat_next, "xhat_next")):
+        _check_vec(g, t, nm)
+    lam = np.zeros(2, dtype=np.float64)
+    check(load().s3_nqz_update(g.handle, ptr(z), ptr(xhat), ptr(x_next), ptr(xhat_next), lam.ctypes.data,
+                               _stream(stream)))
+    return float(lam[0]), float(lam[1])
+
+
+def s3_zeig_options_init(**kw):
+    o = _lib.s3_zeig_options()
+    check(load().s3_zeig_options_init(ctypes.byref(o)))
+    for k, v in kw.items():
+        if not hasattr(o, k):
+            raise TypeError(f"unknown Z-eigenpair option {k}")
+        setattr(o, k, v)
+    return o
+
+
+def s3_zeigenpair(g, x0=None, x_out=None, stream=None, raise_on_noconv=True, **kw):
+    """Z-eigenpair by the shifted power method on the device.  Returns (x, result dict)."""
+    import torch
+    o = s3_zeig_options_init(**kw)
+    if x_out is None:
+        x_out = torch.empty(g.n, dtype=torch.float64, device="cuda")
+    _check_vec(g, x_out, "x_out")
+    if x0 is not None:
+        _check_vec(g, x0, "x0")
+        if x0.dtype != torch.float64:
+            raise TypeError("x0 must be float64")
+    res = _lib.s3_zeig_result()
+    st = load().s3_zeigenpair(g.handle, ctypes.byref(o), ptr(x0), ptr(x_out), ctypes.byref(res), _stream(stream))
+    if st != _lib.S3_OK and not (st == _lib.S3_ENOCONV and not raise_on_noconv):
+        check(st)
+    return x_out, {"lambda": res.lambda_, "iters": res.iters, "converged": res.converged, "seconds": res.seconds,
+                   "status": _lib.status_name(st)}
+
+
+def s3_symmetric_cp(g, R, X0=None, stream=None, **kw):
+    """Greedy rank-R symmetric CP by deflated SS-HOPM.  Returns (lambdas, X (R x n CUDA tensor), iters)."""
+    import torch
+    o = s3_zeig_options_init(**kw)
+    X = torch.empty((int(R), g.n), dtype=torch.float64, device="cuda")
+    if X0 is not None:
+        if (not X0.is_cuda or not X0.is_contiguous() or X0.dtype != torch.float64
+                or tuple(X0.shape) != (int(R), g.n)):
+            raise ValueError("X0 must be a contiguous float64 CUDA tensor of shape (R, n)")
+    lams = np.zeros(int(R), dtype=np.float64)
+    iters = np.zeros(int(R), dtype=np.int32)
+    check(load().s3_symmetric_cp(g.handle, int(R), ctypes.byref(o), ptr(X0), ptr(X), lams.ctypes.data,
+                                 iters.ctypes.data, _stream(stream)))
+    return lams, X, iters
 
 
 def s3_sttsvc_f32_noalloc(n, edge_ptr, members, x, y, rank, stream=None):

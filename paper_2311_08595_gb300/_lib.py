@@ -36,7 +36,7 @@ class s3_options(ctypes.Structure):
                 ("build_ccss", ctypes.c_int32), ("device", ctypes.c_int32), ("thread_max_w", ctypes.c_int32),
                 ("block_threads", ctypes.c_int32), ("order", ctypes.c_int32), ("streams", ctypes.c_int32),
                 ("small_bucket_edges", ctypes.c_int32), ("closed_form_max_s", ctypes.c_int32),
-                ("range_check", ctypes.c_int32), ("reserved", ctypes.c_int32 * 4)]
+                ("range_check", ctypes.c_int32), ("bernoulli", ctypes.c_int32), ("reserved", ctypes.c_int32 * 3)]
 
 
 class s3_format_info(ctypes.Structure):
@@ -61,9 +61,19 @@ class s3_nqz_result(ctypes.Structure):
                 ("seconds", ctypes.c_double)]
 
 
+class s3_zeig_options(ctypes.Structure):
+    _fields_ = [("alpha", ctypes.c_double), ("tol", ctypes.c_double), ("max_iter", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 7)]
+
+
+class s3_zeig_result(ctypes.Structure):
+    _fields_ = [("lambda_", ctypes.c_double), ("iters", ctypes.c_int32), ("converged", ctypes.c_int32),
+                ("seconds", ctypes.c_double), ("reserved", ctypes.c_int32 * 4)]
+
+
 class s3_profile(ctypes.Structure):
     _fields_ = [("edge_ms", ctypes.c_float), ("reduce_ms", ctypes.c_float), ("total_ms", ctypes.c_float),
-                ("launches", ctypes.c_int32), ("reserved", ctypes.c_int32 * 4)]
+                ("launches", ctypes.c_int32), ("bern_ms", ctypes.c_float), ("reserved", ctypes.c_int32 * 3)]
 
 
 class s3_batch_options(ctypes.Structure):
@@ -105,9 +115,15 @@ SIGNATURES = {
     "s3_range_events": (_I32, [_P, ctypes.POINTER(_I64), _I32]),
     "s3_closed_form_query": (_I32, [_P, ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_uint64),
                                     ctypes.POINTER(_I64)]),
+    "s3_bernoulli_query": (_I32, [_P, ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_uint64),
+                                  ctypes.POINTER(_I64)]),
     "s3_sttsvc_profile": (_I32, [_P, _I32, _P, _P, ctypes.POINTER(s3_profile), _P]),
     "s3_nqz_options_init": (_I32, [ctypes.POINTER(s3_nqz_options)]),
     "s3_hcentrality": (_I32, [_P, ctypes.POINTER(s3_nqz_options), _P, _P, ctypes.POINTER(s3_nqz_result), _P]),
+    "s3_nqz_update": (_I32, [_P, _P, _P, _P, _P, _P, _P]),
+    "s3_zeig_options_init": (_I32, [ctypes.POINTER(s3_zeig_options)]),
+    "s3_zeigenpair": (_I32, [_P, ctypes.POINTER(s3_zeig_options), _P, _P, ctypes.POINTER(s3_zeig_result), _P]),
+    "s3_symmetric_cp": (_I32, [_P, _I32, ctypes.POINTER(s3_zeig_options), _P, _P, _P, _P, _P]),
     "s3_sttsvc_f32_noalloc": (_I32, [_I64, _I64, _I32, _P, _P, _P, _P, _P]),
     "s3_batch_options_init": (_I32, [ctypes.POINTER(s3_batch_options)]),
     "s3_batch_create": (_I32, [_I32, _P, _I32, ctypes.POINTER(s3_batch_options), ctypes.POINTER(_P)]),

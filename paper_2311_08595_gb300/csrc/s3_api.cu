@@ -45,6 +45,8 @@ s3_status prepare_device(int dev) {
     S3_CUDA(prepare_edge_kernels_f32());
     S3_CUDA(prepare_edge_kernels_f64());
     S3_CUDA(prepare_edge_kernels_df());
+    S3_CUDA(prepare_edge_bern_f32());
+    S3_CUDA(prepare_edge_bern_f64());
     done[dev] = 1;
     return S3_OK;
 }
@@ -91,49 +93,185 @@ s3_status wait_done(s3_graph_s *g) {
 
 }  // namespace
 
-// Closed-form evaluation of small buckets (s3_closed.cuh): which buckets use it,
-// their constants and rejected-edge lists.  A bucket qualifies for a call type when
-// it has its own launch, 2 <= s <= closed_form_max_s, 2 <= N-1 <= 127, its
-// series kernel takes lists (one thread per edge: W <= thread_max_w), the closed
-// form needs fewer operations than the series, and edges with equal x pass the
-// error gate with a margin of 2 (so that near-uniform inputs are not sent back).
+// Closed-form evaluation of small buckets (s3_closed.cuh): which call types may use
+// it for bucket k (bit 1 = FP32, 2 = FP64), apart from the rule that it needs a launch
+// of its own.  2 <= s <= closed_form_max_s, 2 <= N-1 <= 127, the bucket's series
+// kernel takes lists (one thread per edge: W <= thread_max_w), the closed form needs
+// fewer operations than the series, and edges with equal x pass the error gate with a
+// margin of 2 (so that near-uniform inputs are not sent back).
+int closed_form_mask(const s3_graph_s *g, size_t k) {
+    const int max_s = g->opt.closed_form_max_s == 0 ? kClosedMaxS : std::min(g->opt.closed_form_max_s, kClosedMaxS);
+    const int tmw = (g->opt.thread_max_w <= 0 || g->opt.thread_max_w > 32) ? 32 : g->opt.thread_max_w;
+    const int n = g->N - 1;
+    const HostBucket &hb = g->buckets[k];
+    const int s = hb.s, W = g->N - s + 1;
+    if (max_s < 2 || s < 2 || s > max_s || n < 2 || n > 127 || hb.m <= 0 || W > tmw) return 0;
+    int lg = 0;
+    while ((n >> (lg + 1)) != 0) ++lg;
+    // instructions per edge.  FP32: per subset a two-sum, the powering, its correction and
+    // the accumulations (~11 + 2 log2 n), per edge loads, scaling and stores (~40 + 20 s);
+    // the series kernels: their multiply-adds plus ~3 s W (the size-2 kernel has no products
+    // and little else).  FP64: the FP64 operations alone (the FP64 pipe is the bound).
+    const double subsets = std::ldexp(1.0, s) - 1.0, half = std::ldexp(1.0, s - 1);
+    const double series = s == 2 ? 5.0 * W : (2.0 * s - 5.0) * W * (W + 1) / 2.0 + 3.0 * s * W;
+    const double closed32 = subsets * (11.0 + 2.0 * lg) + s * half + 40.0 + 20.0 * s;
+    const double closed64 = subsets * (2.0 + 2.0 * lg) + s * half + 4.0;
+    // equal x: sum of |terms| over the signed sum, sum_j C(s-1,j) (j+1)^n
+    double pos = 0.0, sgn = 0.0, binom = 1.0;
+    for (int j = 0; j < s; ++j) {
+        const double t = binom * std::pow((double)(j + 1), (double)n);
+        pos += t;
+        sgn += ((s - 1 - j) & 1) ? -t : t;
+        binom = binom * (double)(s - 1 - j) / (double)(j + 1);
+    }
+    const double kappa = sgn > 0.0 ? pos / sgn : 1e300;
+    const double gate32 = ((double)n + half + 4.0) / 128.0;            // C 2^-24 / 2^-17
+    const double gate64 = ((double)s * n + half + 4.0) / 2048.0;       // C 2^-53 / 2^-42
+    int mask = 0;
+    if (closed32 < 0.8 * series && gate32 * kappa <= 0.5) mask |= 1;
+    if (closed64 < 0.8 * series && gate64 * kappa <= 0.5) mask |= 2;
+    return mask;
+}
+
+// beta_k = B_k^+ / k!, the coefficients of z / (1 - e^(-z)), k < 32: the inverse of the
+// series (1 - e^(-z)) / z = sum_k (-1)^k z^k / (k+1)!; beta_k = 0 for odd k >= 3.
+void bernoulli_beta(double beta[32]) {
+    double f[32];
+    double fact = 1.0;
+    for (int k = 0; k < 32; ++k) {
+        fact *= (double)(k + 1);
+        f[k] = ((k & 1) ? -1.0 : 1.0) / fact;
+    }
+    beta[0] = 1.0;
+    for (int m = 1; m < 32; ++m) {
+        double acc = 0.0;
+        for (int k = 1; k <= m; ++k) acc -= f[k] * beta[m - k];
+        beta[m] = (m >= 3 && (m & 1)) ? 0.0 : acc;
+    }
+}
+
+namespace {
+constexpr double kBernKmax32 = 4.0, kBernKmax64 = 64.0;
+}
+
+// Which call types evaluate bucket k in the Bernoulli form (bit 1 = FP32, 2 = FP64):
+// 6 <= s <= 64, W <= thread_max_w, not in closed form for that type, fewer multiply-adds
+// than the prefix/suffix series, and equal x amplified at most kmax / 2.
+int bernoulli_mask(const s3_graph_s *g, size_t k, const double beta[32]) {
+    if (g->opt.bernoulli < 0) return 0;
+    const int tmw = (g->opt.thread_max_w <= 0 || g->opt.thread_max_w > 32) ? 32 : g->opt.thread_max_w;
+    const HostBucket &hb = g->buckets[k];
+    const int s = hb.s, W = g->N - s + 1;
+    if (s < 6 || s > 64 || hb.m <= 0 || W < 1 || W > tmw) return 0;
+    const double series = (2.0 * s - 5.0) * W * (W + 1) / 2.0 + 2.0 * s * W;
+    const double bern = (double)s * W * (W - 1) / 2.0 + 3.0 * s * W;
+    if (!(bern < 0.9 * series)) return 0;
+    // equal x: G = ((e^z - 1)/z)^s on W coefficients, kappa = sum |G[W-1-k] beta_k| / sum G[W-1-k] beta_k
+    std::vector<double> c(W), G(W, 0.0), Gn(W);
+    double fact = 1.0;
+    for (int i = 0; i < W; ++i) {
+        fact *= (double)(i + 1);
+        c[i] = 1.0 / fact;
+    }
+    G[0] = 1.0;
+    for (int r = 0; r < s; ++r) {
+        for (int m = 0; m < W; ++m) {
+            double acc = 0.0;
+            for (int i = 0; i <= m; ++i) acc += c[i] * G[m - i];
+            Gn[m] = acc;
+        }
+        G.swap(Gn);
+    }
+    double sum = 0.0, abs_sum = 0.0;
+    for (int i = 0; i < W; ++i) {
+        sum += G[W - 1 - i] * beta[i];
+        abs_sum += std::fabs(G[W - 1 - i] * beta[i]);
+    }
+    const double kappa = sum > 0.0 ? abs_sum / sum : 1e300;
+    const int cm = closed_form_mask(g, k);
+    int mask = 0;
+    if (!(cm & 1) && kappa <= kBernKmax32 / 2) mask |= 1;
+    if (!(cm & 2) && kappa <= kBernKmax64 / 2) mask |= 2;
+    return mask;
+}
+
+// The device tables of the Bernoulli launch, one per call type (FP32, FP64).
+s3_status plan_bernoulli(s3_graph_s *g) {
+    for (int d = 0; d < 2; ++d) {
+        std::vector<size_t> ks;
+        for (size_t k = 0; k < g->buckets.size(); ++k)
+            if (g->bern_mask[k] & (1 << d)) ks.push_back(k);
+        if (ks.empty()) continue;
+        std::stable_sort(ks.begin(), ks.end(), [&](size_t a, size_t b) { return g->bucket_cost[a] > g->bucket_cost[b]; });
+        std::vector<TailEntry> tab;
+        int64_t blocks = 0;
+        int lane = 0, fb = 0;
+        for (size_t k : ks) {
+            const HostBucket &hb = g->buckets[k];
+            TailEntry t{};
+            t.b.ids = g->d_ids + hb.offset;
+            t.b.slot = g->d_slot + hb.offset;
+            t.b.m = hb.m;
+            t.b.ld = hb.ld;
+            t.b.s = hb.s;
+            t.b.N = g->N;
+            t.b.target = g->target[k];
+            t.b.K = g->K[k];
+            t.b.Km = g->Km[k];
+            t.b.Ke = g->Ke[k];
+            t.W = g->N - hb.s + 1;
+            t.block0 = blocks;
+            blocks += (hb.m + kBernThreads - 1) / kBernThreads;
+            // per lane: the x values, plus (FP64) the member ids staged during the gather
+            lane = std::max(lane, d ? hb.s + (hb.s + 1) / 2 : hb.s);
+            fb = std::max(fb, (int)warp_smem_elems(hb.s, t.W));
+            g->bern_cost[d] += (double)hb.m * ((double)hb.s * t.W * (t.W - 1) / 2.0 + 60.0 * hb.s);
+            tab.push_back(t);
+        }
+        if (bern_smem_bytes(lane, fb, d ? 8 : 4) > kEdgeSmemCap) {
+            // too large for one launch's shared memory: these buckets keep their series kernels
+            for (size_t k : ks) g->bern_mask[k] &= ~(1 << d);
+            g->bern_cost[d] = 0.0;
+            continue;
+        }
+        s3_status st = upload(g, &g->d_bern[d], tab);
+        if (st != S3_OK) return st;
+        g->n_bern[d] = (int32_t)tab.size();
+        g->bern_blocks[d] = blocks;
+        g->bern_lane[d] = lane;
+        g->bern_fb[d] = fb;
+    }
+    double beta[32];
+    bernoulli_beta(beta);
+    for (int k = 0; k < 32; ++k) {
+        g->bern_args.beta64[k] = beta[k];
+        g->bern_args.beta32[k] = (float)beta[k];
+    }
+    g->bern_args.kmax32 = (float)kBernKmax32;
+    g->bern_args.kmax64 = kBernKmax64;
+    if (g->n_bern[0] + g->n_bern[1] > 0) {
+        s3_status st = dev_alloc(g, &g->d_bern_rejected, 1);
+        if (st != S3_OK) return st;
+        if (cudaMemset(g->d_bern_rejected, 0, sizeof(unsigned long long)) != cudaSuccess)
+            return cuda_fail(cudaGetLastError(), "memset");
+        g->bern_args.rejected = g->d_bern_rejected;
+    }
+    return S3_OK;
+}
+
+// Closed-form plan of the handle: buckets with a launch of their own (not in the fused
+// small-bucket launch) that closed_form_mask admits, their constants and rejected-edge lists.
 s3_status plan_closed_form(s3_graph_s *g) {
     const size_t nb = g->buckets.size();
     g->closed_mask.assign(nb, 0);
     g->closed_args.assign(nb, ClosedArgs{});
-    const int max_s = g->opt.closed_form_max_s == 0 ? kClosedMaxS : std::min(g->opt.closed_form_max_s, kClosedMaxS);
-    const int tmw = (g->opt.thread_max_w <= 0 || g->opt.thread_max_w > 32) ? 32 : g->opt.thread_max_w;
     const int n = g->N - 1;
     int64_t list_len = 0;
     std::vector<int64_t> list_off(nb, 0);
     for (size_t k = 0; k < nb; ++k) {
         const HostBucket &hb = g->buckets[k];
-        const int s = hb.s, W = g->N - s + 1;
-        if (max_s < 2 || s < 2 || s > max_s || n < 2 || n > 127 || hb.m <= 0 || g->in_tail[k] || W > tmw) continue;
-        int lg = 0;
-        while ((n >> (lg + 1)) != 0) ++lg;
-        // instructions per edge.  FP32: per subset a two-sum, the powering, its correction and
-        // the accumulations (~11 + 2 log2 n), per edge loads, scaling and stores (~40 + 20 s);
-        // the series kernels: their multiply-adds plus ~3 s W (the size-2 kernel has no products
-        // and little else).  FP64: the FP64 operations alone (the FP64 pipe is the bound).
-        const double subsets = std::ldexp(1.0, s) - 1.0, half = std::ldexp(1.0, s - 1);
-        const double series = s == 2 ? 5.0 * W : (2.0 * s - 5.0) * W * (W + 1) / 2.0 + 3.0 * s * W;
-        const double closed32 = subsets * (11.0 + 2.0 * lg) + s * half + 40.0 + 20.0 * s;
-        const double closed64 = subsets * (2.0 + 2.0 * lg) + s * half + 4.0;
-        // equal x: sum of |terms| over the signed sum, sum_j C(s-1,j) (j+1)^n
-        double pos = 0.0, sgn = 0.0, binom = 1.0;
-        for (int j = 0; j < s; ++j) {
-            const double t = binom * std::pow((double)(j + 1), (double)n);
-            pos += t;
-            sgn += ((s - 1 - j) & 1) ? -t : t;
-            binom = binom * (double)(s - 1 - j) / (double)(j + 1);
-        }
-        const double kappa = sgn > 0.0 ? pos / sgn : 1e300;
-        const double gate32 = ((double)n + half + 4.0) / 128.0;            // C 2^-24 / 2^-17
-        const double gate64 = ((double)s * n + half + 4.0) / 2048.0;       // C 2^-53 / 2^-42
-        int mask = 0;
-        if (closed32 < 0.8 * series && gate32 * kappa <= 0.5) mask |= 1;
-        if (closed64 < 0.8 * series && gate64 * kappa <= 0.5) mask |= 2;
+        if (g->in_tail[k]) continue;
+        const int mask = closed_form_mask(g, k);
         if (!mask) continue;
         g->closed_mask[k] = mask;
         ClosedArgs &c = g->closed_args[k];
@@ -167,7 +305,7 @@ s3_status plan_closed_form(s3_graph_s *g) {
 
 // Launch the per-bucket edge kernels and the reduce for one call.
 s3_status run_edges(s3_graph_s *g, s3_dtype dt, const void *x, void *y, int bias, const int32_t *skip,
-                    cudaStream_t st, cudaEvent_t mid) {
+                    cudaStream_t st, cudaEvent_t mid, cudaEvent_t *bern_ev) {
     int launches = 0;
     const bool seg = g->opt.reduce == S3_REDUCE_SEGMENTED;
     const size_t esz = dt == S3_F32 ? 4 : 8;
@@ -204,6 +342,25 @@ s3_status run_edges(s3_graph_s *g, s3_dtype dt, const void *x, void *y, int bias
         load[best] += cost;
         return g->aux[best];
     };
+    // Bernoulli-form buckets: one launch for all of them (FP32, FP64)
+    const int bd = dt == S3_F32 ? 0 : dt == S3_F64 ? 1 : -1;
+    const bool bern = bd >= 0 && g->n_bern[bd] > 0;
+    bool bern_done = !bern;
+    auto launch_bern = [&]() -> s3_status {
+        bern_done = true;
+        cudaStream_t bs = pick(g->bern_cost[bd]);
+        if (bern_ev) S3_CUDA(cudaEventRecord(bern_ev[0], bs));
+        cudaError_t e = dt == S3_F32 ? launch_edge_bern_f32(g->d_bern[0], g->n_bern[0], g->bern_blocks[0],
+                                                            g->bern_lane[0], g->bern_fb[0], (const float *)x, o,
+                                                            g->bern_args, bs)
+                                     : launch_edge_bern_f64(g->d_bern[1], g->n_bern[1], g->bern_blocks[1],
+                                                            g->bern_lane[1], g->bern_fb[1], (const double *)x, o,
+                                                            g->bern_args, bs);
+        if (e != cudaSuccess) return cuda_fail(e, "Bernoulli launch");
+        if (bern_ev) S3_CUDA(cudaEventRecord(bern_ev[1], bs));
+        ++launches;
+        return S3_OK;
+    };
     // small buckets share one launch (FP32, FP64); the double-float kernels launch per bucket
     const bool fuse = dt != S3_DF64;
     bool tail_done = !fuse || g->n_tail == 0;
@@ -221,7 +378,11 @@ s3_status run_edges(s3_graph_s *g, s3_dtype dt, const void *x, void *y, int bias
     for (size_t r = 0; r < g->bucket_order.size(); ++r) {
         const size_t k = g->bucket_order[r];
         const HostBucket &hb = g->buckets[k];
-        if (hb.m <= 0 || (fuse && g->in_tail[k])) continue;
+        if (hb.m <= 0 || (fuse && g->in_tail[k]) || (bern && (g->bern_mask[k] >> bd & 1))) continue;
+        if (!bern_done && g->bern_cost[bd] >= g->bucket_cost[k]) {
+            s3_status bs = launch_bern();
+            if (bs != S3_OK) return bs;
+        }
         if (!tail_done && g->tail_cost >= g->bucket_cost[k]) {
             s3_status ts = launch_tail();
             if (ts != S3_OK) return ts;
@@ -259,6 +420,10 @@ s3_status run_edges(s3_graph_s *g, s3_dtype dt, const void *x, void *y, int bias
                                        : launch_edge_bucket_df(b, (const double *)x, o, tmw, bth, bs);
         if (e != cudaSuccess) return cuda_fail(e, "edge kernel launch");
         ++launches;
+    }
+    if (!bern_done) {
+        s3_status bs = launch_bern();
+        if (bs != S3_OK) return bs;
     }
     if (!tail_done) {
         s3_status ts = launch_tail();
@@ -451,6 +616,13 @@ s3_status s3_build_format(int64_t n, int64_t m, const int64_t *edge_ptr, const i
     }
     std::stable_sort(g->bucket_order.begin(), g->bucket_order.end(),
                      [&](size_t a, size_t b) { return g->bucket_cost[a] > g->bucket_cost[b]; });
+    // Bernoulli-form buckets (decided before the fused small-bucket launch, which they leave)
+    {
+        double beta[32];
+        bernoulli_beta(beta);
+        g->bern_mask.assign(g->buckets.size(), 0);
+        for (size_t k = 0; k < g->buckets.size(); ++k) g->bern_mask[k] = bernoulli_mask(g, k, beta);
+    }
     // small thread-per-edge buckets: one fused launch.  A bucket of a few thousand
     // edges costs about as much as one edge's latency chain; fused, that latency is
     // paid once per call instead of once per bucket.
@@ -462,7 +634,7 @@ s3_status s3_build_format(int64_t n, int64_t m, const int64_t *edge_ptr, const i
         for (size_t k = 0; k < g->buckets.size(); ++k) {
             const HostBucket &hb = g->buckets[k];
             const int W = g->N - hb.s + 1;
-            if (hb.s < 2 || hb.m <= 0 || hb.m > lim || W > wmax) continue;
+            if (hb.s < 2 || hb.m <= 0 || hb.m > lim || W > wmax || g->bern_mask[k]) continue;
             if (edge_tail_smem_words(hb.s, W, 8) * 4 * (size_t)g->tail_bs > kEdgeSmemCap) continue;
             TailEntry t{};
             t.b.ids = g->d_ids + hb.offset;
@@ -496,6 +668,7 @@ s3_status s3_build_format(int64_t n, int64_t m, const int64_t *edge_ptr, const i
         }
     }
     if ((st = plan_closed_form(g)) != S3_OK) return bail(st);
+    if ((st = plan_bernoulli(g)) != S3_OK) return bail(st);
     g->info.device_bytes = g->device_bytes;
     *out = g;
     return S3_OK;
@@ -591,16 +764,19 @@ s3_status s3_sttsvc_profile(s3_graph_t g, s3_dtype dt, const void *x, void *y, s
     if (g->opt.layout != S3_LAYOUT_EDGE) return fail(S3_ENOTSUP, "profiling covers the edge layout");
     DeviceGuard guard(g->device);
     cudaStream_t st = (cudaStream_t)stream;
-    cudaEvent_t ev[3];
+    cudaEvent_t ev[5];
     for (auto &e : ev) S3_CUDA(cudaEventCreate(&e));
     struct Cleanup {
         cudaEvent_t *e;
         ~Cleanup() {
-            for (int i = 0; i < 3; ++i) cudaEventDestroy(e[i]);
+            for (int i = 0; i < 5; ++i) cudaEventDestroy(e[i]);
         }
     } cleanup{ev};
     S3_CUDA(cudaEventRecord(ev[0], st));
-    s3_status s = run_edges(g, dt, x, y, 0, nullptr, st, ev[1]);
+    // the Bernoulli launch's events are recorded only when it runs (both stay unrecorded otherwise)
+    const int bd = dt == S3_F32 ? 0 : dt == S3_F64 ? 1 : -1;
+    const bool has_bern = bd >= 0 && g->n_bern[bd] > 0;
+    s3_status s = run_edges(g, dt, x, y, 0, nullptr, st, ev[1], has_bern ? ev + 3 : nullptr);
     if (s != S3_OK) return s;
     S3_CUDA(cudaEventRecord(ev[2], st));
     s = mark_done(g, st);
@@ -610,6 +786,7 @@ s3_status s3_sttsvc_profile(s3_graph_t g, s3_dtype dt, const void *x, void *y, s
     S3_CUDA(cudaEventElapsedTime(&prof->edge_ms, ev[0], ev[1]));
     S3_CUDA(cudaEventElapsedTime(&prof->reduce_ms, ev[1], ev[2]));
     S3_CUDA(cudaEventElapsedTime(&prof->total_ms, ev[0], ev[2]));
+    if (has_bern) S3_CUDA(cudaEventElapsedTime(&prof->bern_ms, ev[3], ev[4]));
     prof->launches = g->last_launches;
     return S3_OK;
 }
@@ -653,6 +830,31 @@ s3_status s3_closed_form_query(s3_graph_t g, uint64_t *sizes_f32, uint64_t *size
                 std::memcpy(&t, &cnt[4 * k + 2], sizeof(t));
                 *rejected += (int64_t)t;
             }
+        }
+    }
+    return S3_OK;
+}
+
+s3_status s3_bernoulli_query(s3_graph_t g, uint64_t *sizes_f32, uint64_t *sizes_f64, int64_t *rejected) {
+    if (!g) return fail(S3_EINVAL, "graph is NULL");
+    uint64_t m32 = 0, m64 = 0;
+    for (size_t k = 0; k < g->bern_mask.size(); ++k) {
+        const int s = g->buckets[k].s;  // <= 64 for these buckets
+        if (g->bern_mask[k] & 1) m32 |= 1ull << (s - 1);
+        if (g->bern_mask[k] & 2) m64 |= 1ull << (s - 1);
+    }
+    if (sizes_f32) *sizes_f32 = m32;
+    if (sizes_f64) *sizes_f64 = m64;
+    if (rejected) {
+        *rejected = 0;
+        if (g->d_bern_rejected) {
+            DeviceGuard guard(g->device);
+            s3_status s = wait_done(g);
+            if (s != S3_OK) return s;
+            unsigned long long c = 0;
+            S3_CUDA(cudaMemcpyAsync(&c, g->d_bern_rejected, sizeof(c), cudaMemcpyDeviceToHost, g->qstream));
+            S3_CUDA(cudaStreamSynchronize(g->qstream));
+            *rejected = (int64_t)c;
         }
     }
     return S3_OK;

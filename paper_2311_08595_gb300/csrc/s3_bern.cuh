@@ -1,0 +1,234 @@
+// Leave-one-out through the Bernoulli series: all contributions of an edge from
+// one product over its members.
+//
+// For an edge e = (v_1 .. v_s) at rank N (window W = N - s + 1) write
+//     Ebar(x t) = e^(x t) - 1 = x t g_x(t),   g_x(t) = sum_k x^k t^k / (k+1)!,
+// so F_e = prod_j Ebar(x_j t) = t^s (prod_j x_j) G(t) with G = prod_j g_{x_j}.
+// Since E = e^(x t) and E(x t) / Ebar(x t) = 1 / (1 - e^(-x t)), which is
+// (1 / (x t)) sum_k beta_k x^k t^k with beta_k = B_k^+ / k! (the Bernoulli
+// numbers, B_1 = +1/2), the per-(edge, node) value of Algorithm 2 is
+//     [t^(N-1)] E(x_i t) prod_{j != i} Ebar(x_j t)
+//         = (prod_{j != i} x_j) * sum_{k=0}^{W-1} G[W-1-k] beta_k x_i^k.
+// G takes one truncated product per member (W(W-1)/2 multiply-adds each), and
+// every member then needs one short polynomial in x_i: about s W^2 / 2
+// operations per edge against the prefix/suffix scheme's (2s - 5) W^2 / 2, and
+// no stored prefix windows (per thread only the edge's x and scalar prefix
+// products live in shared memory).
+//
+// The coefficients of G are sums of positive terms (x >= 0), but beta_k
+// alternates in sign for even k >= 4, so the final sum can cancel.  With
+// P = the sum of its positive terms and Q = the magnitude of its negative ones,
+// the value is P - Q and kappa = (P + Q) / (P - Q) bounds how much the relative
+// error of G and of the sum is amplified.  An edge is accepted when every
+// member has kappa <= kappa_max (BernArgs; 4 for FP32, 64 for FP64) and all its
+// x are >= 0; otherwise the warp recomputes it with the prefix/suffix series
+// (warp_edge_compute), so results are never less accurate than kappa_max times
+// the positive-term error.  For near-equal x, kappa stays below 1.2 for s >= 6
+// at rank 25 (below 2.2 when one member is twice the others).
+#pragma once
+
+#include "s3_series.cuh"
+
+namespace s3 {
+
+// The Bernoulli sum of one member, split into its positive part P (k = 0, 1 and
+// k = 2 mod 4) and the magnitude Q of its negative part (k = 0 mod 4, k >= 4):
+// H[k] = G[W-1-k] beta_k, Horner in x^4 for each residue class.
+template <typename T, int W>
+__device__ __forceinline__ void bern_eval(const T (&H)[W], T xi, T &P, T &Q) {
+    const T x2 = xi * xi, x4 = x2 * x2;
+    T p2 = T(0);
+    if constexpr (W > 2) {
+#pragma unroll
+        for (int k = 2 + 4 * ((W - 1 - 2) / 4); k >= 2; k -= 4) p2 = Arith<T>::fma_(p2, x4, H[k]);
+    }
+    T p = H[0];
+    if constexpr (W > 1) p = Arith<T>::fma_(H[1], xi, p);
+    P = Arith<T>::fma_(p2, x2, p);
+    T q = T(0);
+    if constexpr (W > 4) {
+#pragma unroll
+        for (int k = 4 + 4 * ((W - 1 - 4) / 4); k >= 4; k -= 4) q = Arith<T>::fma_(q, x4, -H[k]);
+        q = q * x4;
+    }
+    Q = q;
+}
+
+template <typename T> __device__ __forceinline__ T bern_beta(const BernArgs &c, int k);
+template <> __device__ __forceinline__ float bern_beta<float>(const BernArgs &c, int k) { return c.beta32[k]; }
+template <> __device__ __forceinline__ double bern_beta<double>(const BernArgs &c, int k) { return c.beta64[k]; }
+template <typename T> __device__ __forceinline__ T bern_kmax(const BernArgs &c);
+template <> __device__ __forceinline__ float bern_kmax<float>(const BernArgs &c) { return c.kmax32; }
+template <> __device__ __forceinline__ double bern_kmax<double>(const BernArgs &c) { return c.kmax64; }
+
+// The series fallback for an edge the gate rejected (kept out of line: it is rarely
+// taken, and inlined into every window's code it would crowd the instruction cache).
+template <typename T>
+__device__ __noinline__ void bern_fallback(const EdgeBucketArgs &b, const T *__restrict__ x, const EdgeOutArgs &o,
+                                           int64_t e, int W, T *fb) {
+    warp_edge_compute<T>(b, x, o, e, W, fb);
+}
+
+// One edge per thread (e < b.m when valid).  lane_base: this warp's region, element i
+// of lane l at i * kLS + l: the edge's x values, then (FP64 only) the member ids staged
+// while x is gathered (FP32 stages each id in its own x slot, which the gather then
+// overwrites).  Shared memory is kept to that -- the x gathers also use the L1 cache,
+// which the rest of the shared-memory carve-out would take away.  fb: the warp's region
+// for the series fallback.
+template <typename T, int W, bool BUF>
+__device__ __forceinline__ void bern_edge(const EdgeBucketArgs &b, const T *__restrict__ x, const EdgeOutArgs &o,
+                                          const BernArgs &c, int64_t e, bool valid, T *lane_base, T *fb) {
+    const int lane = threadIdx.x & 31;
+    const int s = b.s;
+    T *xs = lane_base + lane;
+    int32_t *idst = sizeof(T) == 4 ? reinterpret_cast<int32_t *>(lane_base) + lane
+                                   : reinterpret_cast<int32_t *>(lane_base + s * kLS) + lane;
+    bool ok = valid;
+    int p = 0;
+    if (valid) {
+        for (int i = 0; i < s; ++i) cp_async<4>(idst + i * kLS, b.ids + (int64_t)i * b.ld + e);
+        cp_async_commit();
+        cp_async_wait_all();
+        for (int i = 0; i < s; ++i) cp_async<(int)sizeof(T)>(xs + i * kLS, x + idst[i * kLS]);
+        cp_async_commit();
+        cp_async_wait_all();
+        T S = T(0);
+        bool pos = true;
+        for (int i = 0; i < s; ++i) {
+            const T v = xs[i * kLS];
+            S += Arith<T>::absv(v);
+            pos &= v > T(0);
+        }
+        p = scale_exponent<T>(S, b.target);
+        const T g = Arith<T>::pow2(p);
+        // G = g_{x_1} (its coefficients x^k / (k+1)!), then times g_{x_i}, i = 2..s;
+        // P = the product of all (scaled) x
+        T G[W];
+        T prod;
+        {
+            const T x0 = xs[0] * g;
+            xs[0] = x0;
+            prod = x0;
+            G[0] = T(1);
+#pragma unroll
+            for (int k = 1; k < W; ++k) G[k] = G[k - 1] * (x0 * Num<T>::recip(k + 1));
+        }
+        for (int i = 1; i < s; ++i) {
+            const T xi = xs[i * kLS] * g;
+            xs[i * kLS] = xi;
+            prod *= xi;
+            T r[W];
+#pragma unroll
+            for (int k = 1; k < W; ++k) r[k] = xi * Num<T>::recip(k + 1);
+            // G[m] <- G[m] + r_1 (G[m-1] + r_2 (G[m-2] + ... + r_m G[0])), top down in place
+#pragma unroll
+            for (int m = W - 1; m >= 1; --m) {
+                T t = G[0];
+#pragma unroll
+                for (int j = 1; j <= m; ++j) t = Arith<T>::fma_(r[m - j + 1], t, G[j]);
+                G[m] = t;
+            }
+        }
+        T H[W];
+#pragma unroll
+        for (int k = 0; k < W; ++k) H[k] = G[W - 1 - k] * bern_beta<T>(c, k);
+        const T kmax = bern_kmax<T>(c);
+        // every member: the Bernoulli sum (gate), times prod_{j != i} x_j = P / x_i (all x > 0)
+        for (int i = 0; i < s; ++i) {
+            const T xi = xs[i * kLS];
+            T Pp, Q;
+            bern_eval<T, W>(H, xi, Pp, Q);
+            const T v = Pp - Q;
+            ok &= (Pp + Q) <= kmax * v;
+            xs[i * kLS] = v * (prod / xi);
+        }
+        ok &= pos;
+    }
+    const unsigned rej = __ballot_sync(0xffffffffu, valid && !ok);
+    if (valid && ok) {
+        const EdgeScale<T> sc = edge_scale(b, o, p, T(0));
+        int nbad = 0;
+        // the targets (incidence slots, or node ids in the atomic modes) in chunks of eight
+        // independent loads, so that each store does not wait for its own round trip
+        constexpr int kChunk = 8;
+        for (int i0 = 0; i0 < s; i0 += kChunk) {
+            int tv[kChunk];
+#pragma unroll
+            for (int j = 0; j < kChunk; ++j)
+                tv[j] = i0 + j < s ? __ldg((BUF ? b.slot : b.ids) + (int64_t)(i0 + j) * b.ld + e) : 0;
+#pragma unroll
+            for (int j = 0; j < kChunk; ++j) {
+                const int i = i0 + j;
+                if (i >= s) break;
+                const T val = xs[i * kLS];
+                const int t = tv[j];
+                if (sc.fast) {
+                    emit_fast<T, BUF>(o, t, val, sc.mult, nbad);
+                } else {
+                    // scaled x of the member (its exponent sets the per-node bias of NQZ)
+                    const T xhat = __ldg(x + __ldg(b.ids + (int64_t)i * b.ld + e)) * Arith<T>::pow2(p);
+                    emit_value<T, BUF>(b, o, t, t, val, p, xhat);
+                }
+            }
+        }
+        if (nbad && o.range_events) atomicAdd(o.range_events, (unsigned long long)nbad);
+    }
+    // edges that failed the gate (or hold an x <= 0): the whole warp recomputes each with
+    // the series
+    if (rej && lane == 0 && c.rejected) atomicAdd(c.rejected, (unsigned long long)__popc(rej));
+    for (unsigned r = rej; r; r &= r - 1) {
+        const int64_t ee = __shfl_sync(0xffffffffu, e, __ffs(r) - 1);
+        bern_fallback<T>(b, x, o, ee, W, fb);
+    }
+}
+
+// All Bernoulli buckets of a call in one launch: block ranges map to buckets
+// (TailEntry::block0 ascending), one edge per thread.  Per warp: lane_elems
+// values per lane, then fb_elems values for the series fallback.
+template <typename T, bool BUF>
+__global__ void __launch_bounds__(kBernThreads, sizeof(T) == 4 ? 7 : 3) edge_bern_kernel(const TailEntry *__restrict__ tab, int ntab,
+                                                                 int lane_elems, int fb_elems,
+                                                                 const T *__restrict__ x, EdgeOutArgs o, BernArgs c) {
+    if (o.skip && *o.skip) return;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    int k = 0;
+    while (k + 1 < ntab && tab[k + 1].block0 <= (int64_t)blockIdx.x) ++k;
+    const EdgeBucketArgs b = tab[k].b;
+    const int64_t e = ((int64_t)blockIdx.x - tab[k].block0) * blockDim.x + threadIdx.x;
+    const bool valid = e < b.m;
+    if (__all_sync(0xffffffffu, !valid)) return;
+    const size_t warp_elems = (size_t)kLS * lane_elems + (size_t)fb_elems;
+    T *base = reinterpret_cast<T *>(smem_raw) + (size_t)(threadIdx.x >> 5) * warp_elems;
+    T *fb = base + (size_t)kLS * lane_elems;
+    switch (tab[k].W) {
+#define S3_BERN_CASE(w) \
+    case w: bern_edge<T, w, BUF>(b, x, o, c, e, valid, base, fb); break;
+        S3_W_CASES(S3_BERN_CASE)
+#undef S3_BERN_CASE
+        default: break;
+    }
+}
+
+template <typename T>
+cudaError_t launch_edge_bern_t(const TailEntry *tab, int ntab, int64_t nblocks, int lane_elems, int fb_elems,
+                               const T *x, const EdgeOutArgs &o, const BernArgs &c, cudaStream_t st) {
+    if (ntab <= 0 || nblocks <= 0) return cudaSuccess;
+    const size_t smem = bern_smem_bytes(lane_elems, fb_elems, sizeof(T));
+    if (smem > kEdgeSmemCap || nblocks > INT32_MAX) return cudaErrorInvalidConfiguration;
+    if (o.mode == kOutBuffer)
+        edge_bern_kernel<T, true><<<(unsigned)nblocks, kBernThreads, smem, st>>>(tab, ntab, lane_elems, fb_elems, x, o, c);
+    else
+        edge_bern_kernel<T, false><<<(unsigned)nblocks, kBernThreads, smem, st>>>(tab, ntab, lane_elems, fb_elems, x, o, c);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t prepare_edge_bern_t() {
+    cudaError_t e = cudaFuncSetAttribute(edge_bern_kernel<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)kEdgeSmemCap);
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(edge_bern_kernel<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)kEdgeSmemCap);
+}
+
+}  // namespace s3

@@ -68,6 +68,7 @@ struct s3_graph_s {
     double *d_red = nullptr;        // reduction partials
     int32_t *d_flags = nullptr;     // [0] done, [1] phase-switch, ...
     double *d_hist = nullptr;       // per-iteration (lmin, lmax)
+    double *d_zeig = nullptr;       // SS-HOPM / symmetric CP reduction partials and scalars
     int32_t hist_cap = 0;
     int64_t first_isolated = -1;    // a node of degree 0 (NQZ rejects the handle), or -1
     // captured NQZ passes, kept for later calls with the same settings: one per series type
@@ -107,6 +108,17 @@ struct s3_graph_s {
     // bucket's rejected-edge list, d_closed_count four counters per bucket ([0] list
     // length, cleared at the start of every call; [2..3] rejected edges in total)
     std::vector<int32_t> closed_mask;
+    // Bernoulli-form buckets (s3_bern.cuh): per bucket a bit mask of the call types that use
+    // it (1 = FP32, 2 = FP64); per call type a device table of those buckets (ascending
+    // block0, heaviest first) for the one launch that evaluates them all
+    std::vector<int32_t> bern_mask;
+    s3::TailEntry *d_bern[2] = {nullptr, nullptr};
+    int32_t n_bern[2] = {0, 0};
+    int64_t bern_blocks[2] = {0, 0};
+    int32_t bern_lane[2] = {0, 0}, bern_fb[2] = {0, 0};
+    double bern_cost[2] = {0.0, 0.0};
+    s3::BernArgs bern_args{};
+    unsigned long long *d_bern_rejected = nullptr;
     std::vector<s3::ClosedArgs> closed_args;
     int32_t *d_closed_list = nullptr;
     int32_t *d_closed_count = nullptr;
@@ -151,9 +163,10 @@ s3_status cuda_fail(cudaError_t e, const char *what);
 s3_status prepare_device(int dev);
 // Record the completion of a call's work on st (skipped while st is being captured).
 s3_status mark_done(s3_graph_s *g, cudaStream_t st);
-// mid (optional) is recorded on st between the edge kernels and the reduce
+// mid (optional) is recorded on st between the edge kernels and the reduce; bern (optional,
+// two events) around the Bernoulli launch on the stream it runs on
 s3_status run_edges(s3_graph_s *g, s3_dtype dt, const void *x, void *y, int bias, const int32_t *skip,
-                    cudaStream_t st, cudaEvent_t mid = nullptr);
+                    cudaStream_t st, cudaEvent_t mid = nullptr, cudaEvent_t *bern = nullptr);
 s3_status run_ccss(s3_graph_s *g, s3_dtype dt, const void *x, void *y, int bias, const int32_t *skip,
                    cudaStream_t st);
 s3_status upload_ccss(s3_graph_s *g, const HostFormat &f);

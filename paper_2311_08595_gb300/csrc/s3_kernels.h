@@ -46,6 +46,29 @@ struct TailEntry {
     int64_t block0;
 };
 
+// Elements per warp of the shared memory of one warp-per-edge series evaluation
+// (warp_edge_compute in s3_series.cuh): Xs[s] | C[s] | Pre[(s-2) W] | 4 windows of W.
+__host__ __device__ constexpr int64_t warp_smem_elems(int s, int W) {
+    return ((2 * (int64_t)s + (int64_t)(s > 2 ? s - 2 : 0) * W + 4 * (int64_t)W) + 3) / 4 * 4;
+}
+
+// Constants of the Bernoulli-series kernels (s3_bern.cuh): beta_k = B_k^+ / k!
+// (Bernoulli numbers, B_1 = +1/2; zero for odd k >= 3), k < 32, and the largest
+// accepted amplification (P + Q) / (P - Q) of the alternating sum.
+struct BernArgs {
+    float beta32[32];
+    double beta64[32];
+    float kmax32;
+    double kmax64;
+    unsigned long long *rejected;   // running count of edges sent back to the series
+};
+constexpr int kBernThreads = 128;   // threads per block of the Bernoulli launch (one edge each)
+// Dynamic shared memory of a Bernoulli launch: per warp 32 lanes x lane_elems values plus
+// fb_elems values for the series fallback.
+inline size_t bern_smem_bytes(int lane_elems, int fb_elems, size_t value_bytes) {
+    return (size_t)(kBernThreads / 32) * ((size_t)32 * lane_elems + (size_t)fb_elems) * value_bytes;
+}
+
 enum OutMode : int32_t {
     kOutBuffer = 0,       // out[slot] = c
     kOutAtomic = 1,       // out[v] += c (atomics)
@@ -100,6 +123,14 @@ cudaError_t launch_edge_closed_f32(const EdgeBucketArgs &b, const float *x, cons
 cudaError_t launch_edge_closed_f64(const EdgeBucketArgs &b, const double *x, const EdgeOutArgs &o,
                                    const ClosedArgs &c, cudaStream_t st);
 constexpr int kClosedMaxS = 6;
+// One launch of every Bernoulli bucket of a call (tab: device, ascending block0,
+// kBernThreads threads per block, one edge per thread).  FP32 and FP64.
+cudaError_t launch_edge_bern_f32(const TailEntry *tab, int ntab, int64_t nblocks, int lane_elems, int fb_elems,
+                                 const float *x, const EdgeOutArgs &o, const BernArgs &c, cudaStream_t st);
+cudaError_t launch_edge_bern_f64(const TailEntry *tab, int ntab, int64_t nblocks, int lane_elems, int fb_elems,
+                                 const double *x, const EdgeOutArgs &o, const BernArgs &c, cudaStream_t st);
+cudaError_t prepare_edge_bern_f32();
+cudaError_t prepare_edge_bern_f64();
 // One-time per-device set-up (shared-memory limits of the kernels).
 cudaError_t prepare_edge_kernels_f32();
 cudaError_t prepare_edge_kernels_f64();

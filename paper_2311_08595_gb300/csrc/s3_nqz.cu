@@ -19,6 +19,7 @@
 // the same tolerance, iteration cap and graph length.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <chrono>
 #include <cmath>
 #include <cstring>
@@ -33,7 +34,7 @@ namespace {
 constexpr int kNqzThreads = 256;
 constexpr int kNqzBlocks = 592;   // 4 x 148..152 SMs; fixed so sums are reproducible
 
-// flags: [0] done, [1] iterations, [2] hit max_iter, [3] range trouble
+// flags: [0] done, [1] iterations, [2] hit max_iter, [3] range trouble, [4] block counter
 enum { F_DONE = 0, F_ITERS = 1, F_MAXED = 2, F_RANGE = 3 };
 
 // r = a^(1/k) for a > 0: FP32 guess then one Newton step in FP64.
@@ -57,121 +58,142 @@ __device__ __forceinline__ double root_k(double a, int k) {
     return r * Arith<double>::pow2(q);
 }
 
-template <typename T>
-__device__ __forceinline__ void block_sum_store(double v, double *out) {
-    __shared__ double sh[kNqzThreads / 32];
+// flags[F_COUNT]: blocks of the current after-kernel that have stored their partials
+enum { F_COUNT = 4 };
+
+// Sum (fixed order: warp trees, then warps in order) of one value per thread; thread 0 gets it.
+__device__ __forceinline__ double block_sum(double v, double *sh) {
 #pragma unroll
     for (int d = 16; d > 0; d >>= 1) v += __shfl_down_sync(0xffffffffu, v, d);
+    __syncthreads();
     if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = v;
     __syncthreads();
-    if (threadIdx.x == 0) {
-        double t = 0.0;
+    double t = 0.0;
+    if (threadIdx.x == 0)
         for (int w = 0; w < kNqzThreads / 32; ++w) t += sh[w];
-        *out = t;
-    }
+    return t;
 }
 
-// u_v = zt_v^(1/(N-1)) 2^(e_v); partial 1-norms per block
-template <typename TZ, typename TX>
-__global__ void __launch_bounds__(kNqzThreads) nqz_root_kernel(const TZ *__restrict__ zt, const TX *__restrict__ xin,
-                                                               int64_t n, int k, double *__restrict__ u,
-                                                               double *__restrict__ partial, int32_t *flags) {
-    if (flags[F_DONE]) return;
-    double acc = 0.0;
-    for (int64_t v = (int64_t)blockIdx.x * kNqzThreads + threadIdx.x; v < n; v += (int64_t)gridDim.x * kNqzThreads) {
-        double z = (double)zt[v];
-        int e = Arith<TX>::expo(xin[v]);
-        double r = root_k(z, k) * Arith<double>::pow2(e);
-        if (!(z > 0.0) || !isfinite(z)) flags[F_RANGE] = 1;
-        u[v] = r;
-        acc += r;
-    }
-    block_sum_store<double>(acc, partial + blockIdx.x);
-}
-
-// x = u / ||u||_1 (FP64) and its FP32 copy
-__global__ void __launch_bounds__(kNqzThreads) nqz_normalize_kernel(const double *__restrict__ u, int64_t n,
-                                                                    const double *__restrict__ partial, int nparts,
-                                                                    double *__restrict__ x64, float *__restrict__ x32,
-                                                                    int32_t *flags) {
-    if (flags[F_DONE]) return;
-    __shared__ double inv;
-    if (threadIdx.x == 0) {
-        double t = 0.0;
-        for (int i = 0; i < nparts; ++i) t += partial[i];
-        inv = 1.0 / t;
-    }
-    __syncthreads();
-    for (int64_t v = (int64_t)blockIdx.x * kNqzThreads + threadIdx.x; v < n; v += (int64_t)gridDim.x * kNqzThreads) {
-        double xv = u[v] * inv;
-        x64[v] = xv;
-        x32[v] = (float)xv;
-    }
-}
-
-// ratios zt_v / m_v^(N-1) (m_v = x_v 2^-e_v of the vector the TTSV1 call used); partial min/max
-template <typename T>
-__global__ void __launch_bounds__(kNqzThreads) nqz_ratio_kernel(const T *__restrict__ zt, const T *__restrict__ xin,
-                                                                int64_t n, int k, double *__restrict__ partial,
-                                                                int32_t *flags) {
-    if (flags[F_DONE]) return;
-    double lo = INFINITY, hi = -INFINITY;
-    for (int64_t v = (int64_t)blockIdx.x * kNqzThreads + threadIdx.x; v < n; v += (int64_t)gridDim.x * kNqzThreads) {
-        double xv = (double)xin[v];
-        int e = Arith<double>::expo(xv);
-        double m = xv * Arith<double>::pow2(-e);
-        double pk = 1.0, base = m;
-        for (int q = k; q > 0; q >>= 1) {
-            if (q & 1) pk *= base;
-            base *= base;
-        }
-        double r = (double)zt[v] / pk;
-        if (!isfinite(r) || !(r > 0.0)) flags[F_RANGE] = 1;
-        lo = fmin(lo, r);
-        hi = fmax(hi, r);
-    }
-    __shared__ double sl[kNqzThreads / 32], sh[kNqzThreads / 32];
+__device__ __forceinline__ void block_minmax(double &lo, double &hi, double *sl, double *sh) {
 #pragma unroll
     for (int d = 16; d > 0; d >>= 1) {
         lo = fmin(lo, __shfl_down_sync(0xffffffffu, lo, d));
         hi = fmax(hi, __shfl_down_sync(0xffffffffu, hi, d));
     }
+    __syncthreads();
     if ((threadIdx.x & 31) == 0) {
         sl[threadIdx.x >> 5] = lo;
         sh[threadIdx.x >> 5] = hi;
     }
     __syncthreads();
-    if (threadIdx.x == 0) {
+    if (threadIdx.x == 0)
         for (int w = 1; w < kNqzThreads / 32; ++w) {
             lo = fmin(lo, sl[w]);
             hi = fmax(hi, sh[w]);
         }
-        partial[2 * blockIdx.x] = lo;
-        partial[2 * blockIdx.x + 1] = hi;
+}
+
+// Everything Algorithm 1 does with one S^3TTVc result z (biased: zt) of the iterate x:
+//  * unless `first`: the ratios zt_v / m_v^(N-1) (= z_v / x_v^(N-1), m_v = x_v 2^-e_v) and
+//    their min and max -- lambda_min, lambda_max of this pass -- and the stopping test;
+//  * the next iterate before normalisation, u_v = zt_v^(1/(N-1)) 2^e_v (= z_v^(1/(N-1))),
+//    and its 1-norm, whose inverse goes to scal[0] for nqz_normalize_kernel.
+// Each block stores partial sums / minima / maxima; the last block to finish (a counter in
+// flags) reduces them in a fixed order with all its threads, so the results do not depend
+// on which block is last.
+template <typename T>
+__global__ void __launch_bounds__(kNqzThreads) nqz_after_kernel(const T *__restrict__ zt, const T *__restrict__ xin,
+                                                                int64_t n, int k, int first, double *__restrict__ u,
+                                                                double *__restrict__ part_sum,
+                                                                double *__restrict__ part_mm, double *__restrict__ scal,
+                                                                double tol, int max_iter, double *__restrict__ hist,
+                                                                int hist_cap, int32_t *flags) {
+    if (flags[F_DONE]) return;
+    __shared__ double sa[kNqzThreads / 32], sb[kNqzThreads / 32];
+    __shared__ int last;
+    double acc = 0.0, lo = INFINITY, hi = -INFINITY;
+    bool bad = false;
+    for (int64_t v = (int64_t)blockIdx.x * kNqzThreads + threadIdx.x; v < n; v += (int64_t)gridDim.x * kNqzThreads) {
+        const double z = (double)zt[v];
+        const double xv = (double)xin[v];
+        const int e = Arith<double>::expo(xv);
+        const double r = root_k(z, k) * Arith<double>::pow2(e);
+        bad |= !(z > 0.0) || !isfinite(z);
+        u[v] = r;
+        acc += r;
+        if (!first) {
+            const double m = xv * Arith<double>::pow2(-e);
+            double pk = 1.0, base = m;
+            for (int q = k; q > 0; q >>= 1) {
+                if (q & 1) pk *= base;
+                base *= base;
+            }
+            const double ratio = z / pk;
+            bad |= !isfinite(ratio) || !(ratio > 0.0);
+            lo = fmin(lo, ratio);
+            hi = fmax(hi, ratio);
+        }
+    }
+    const int any_bad = __syncthreads_or(bad);
+    const double bsum = block_sum(acc, sa);
+    if (!first) block_minmax(lo, hi, sa, sb);
+    if (threadIdx.x == 0) {
+        if (any_bad) flags[F_RANGE] = 1;
+        part_sum[blockIdx.x] = bsum;
+        if (!first) {
+            part_mm[2 * blockIdx.x] = lo;
+            part_mm[2 * blockIdx.x + 1] = hi;
+        }
+        __threadfence();
+        last = atomicAdd(flags + F_COUNT, 1) == (int)gridDim.x - 1;
+    }
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    // the last block: reduce the partials (L2 loads: other blocks wrote them)
+    acc = 0.0;
+    lo = INFINITY;
+    hi = -INFINITY;
+    for (int i = threadIdx.x; i < (int)gridDim.x; i += kNqzThreads) {
+        acc += __ldcg(part_sum + i);
+        if (!first) {
+            lo = fmin(lo, __ldcg(part_mm + 2 * i));
+            hi = fmax(hi, __ldcg(part_mm + 2 * i + 1));
+        }
+    }
+    const double tot = block_sum(acc, sa);
+    if (!first) block_minmax(lo, hi, sa, sb);
+    if (threadIdx.x == 0) {
+        scal[0] = 1.0 / tot;
+        flags[F_COUNT] = 0;
+        if (!first) {
+            const int it = __ldcg(flags + F_ITERS);
+            if (it < hist_cap) {
+                hist[2 * it] = lo;
+                hist[2 * it + 1] = hi;
+            }
+            flags[F_ITERS] = it + 1;
+            if ((hi - lo) / lo < tol) flags[F_DONE] = 1;
+            if (it + 1 >= max_iter) {
+                flags[F_DONE] = 1;
+                flags[F_MAXED] = 1;
+            }
+        }
+        if (__ldcg(flags + F_RANGE)) flags[F_DONE] = 1;
     }
 }
 
-// convergence test of Algorithm 1; records (lambda_min, lambda_max) per iteration
-__global__ void nqz_check_kernel(const double *__restrict__ partial, int nparts, double tol, int max_iter,
-                                 double *__restrict__ hist, int hist_cap, int32_t *flags) {
+// x = u / ||u||_1 (FP64) and its FP32 copy
+__global__ void __launch_bounds__(kNqzThreads) nqz_normalize_kernel(const double *__restrict__ u, int64_t n,
+                                                                    const double *__restrict__ scal,
+                                                                    double *__restrict__ x64, float *__restrict__ x32,
+                                                                    int32_t *flags) {
     if (flags[F_DONE]) return;
-    if (threadIdx.x != 0) return;
-    double lo = INFINITY, hi = -INFINITY;
-    for (int i = 0; i < nparts; ++i) {
-        lo = fmin(lo, partial[2 * i]);
-        hi = fmax(hi, partial[2 * i + 1]);
-    }
-    int it = flags[F_ITERS];
-    if (it < hist_cap) {
-        hist[2 * it] = lo;
-        hist[2 * it + 1] = hi;
-    }
-    flags[F_ITERS] = it + 1;
-    if ((hi - lo) / lo < tol) flags[F_DONE] = 1;
-    if (flags[F_RANGE]) flags[F_DONE] = 1;
-    if (it + 1 >= max_iter) {
-        flags[F_DONE] = 1;
-        flags[F_MAXED] = 1;
+    const double inv = scal[0];
+    for (int64_t v = (int64_t)blockIdx.x * kNqzThreads + threadIdx.x; v < n; v += (int64_t)gridDim.x * kNqzThreads) {
+        const double xv = u[v] * inv;
+        x64[v] = xv;
+        x32[v] = (float)xv;
     }
 }
 
@@ -206,39 +228,320 @@ s3_status ensure_nqz_scratch(s3_graph_s *g, int hist_cap) {
 struct NqzBufs {
     double *x64, *u, *z64;
     float *x32, *z32;
-    double *part_sum, *part_mm;
+    double *part_sum, *part_mm, *scal;
     int32_t *flags;
 };
 
-// One repeat-body pass.  tz: type of the z from the previous pass; tc: type of this pass's TTSV1.
-s3_status nqz_step(s3_graph_s *g, const NqzBufs &b, s3_dtype tz, s3_dtype tc, double tol, int max_iter,
-                   cudaStream_t st) {
+// The kernel that takes the S^3TTVc result of type dt (see nqz_after_kernel).
+s3_status nqz_after(s3_graph_s *g, const NqzBufs &b, s3_dtype dt, bool first, double tol, int max_iter,
+                    cudaStream_t st) {
     const int k = g->N - 1;
-    const int64_t n = g->n;
-    if (tz == S3_F32)
-        nqz_root_kernel<float, float><<<kNqzBlocks, kNqzThreads, 0, st>>>(b.z32, b.x32, n, k, b.u, b.part_sum, b.flags);
+    if (dt == S3_F32)
+        nqz_after_kernel<float><<<kNqzBlocks, kNqzThreads, 0, st>>>(b.z32, b.x32, g->n, k, first ? 1 : 0, b.u,
+                                                                     b.part_sum, b.part_mm, b.scal, tol, max_iter,
+                                                                     g->d_hist, g->hist_cap, b.flags);
     else
-        nqz_root_kernel<double, double><<<kNqzBlocks, kNqzThreads, 0, st>>>(b.z64, b.x64, n, k, b.u, b.part_sum,
-                                                                             b.flags);
+        nqz_after_kernel<double><<<kNqzBlocks, kNqzThreads, 0, st>>>(b.z64, b.x64, g->n, k, first ? 1 : 0, b.u,
+                                                                      b.part_sum, b.part_mm, b.scal, tol, max_iter,
+                                                                      g->d_hist, g->hist_cap, b.flags);
     S3_CUDA(cudaGetLastError());
-    nqz_normalize_kernel<<<kNqzBlocks, kNqzThreads, 0, st>>>(b.u, n, b.part_sum, kNqzBlocks, b.x64, b.x32, b.flags);
+    return S3_OK;
+}
+
+// One repeat-body pass of Algorithm 1: normalise the pending root vector u into x, z =
+// S^3TTVc(x) with series of type tc, then ratios, bracket, test and the next u.
+s3_status nqz_step(s3_graph_s *g, const NqzBufs &b, s3_dtype tc, double tol, int max_iter, cudaStream_t st) {
+    const int64_t n = g->n;
+    nqz_normalize_kernel<<<kNqzBlocks, kNqzThreads, 0, st>>>(b.u, n, b.scal, b.x64, b.x32, b.flags);
     S3_CUDA(cudaGetLastError());
     s3_status s;
-    if (tc == S3_F32) {
+    if (tc == S3_F32)
         s = g->opt.layout == S3_LAYOUT_CCSS && g->has_ccss ? run_ccss(g, S3_F32, b.x32, b.z32, 1, b.flags, st)
                                                             : run_edges(g, S3_F32, b.x32, b.z32, 1, b.flags, st);
-        if (s != S3_OK) return s;
-        nqz_ratio_kernel<float><<<kNqzBlocks, kNqzThreads, 0, st>>>(b.z32, b.x32, n, k, b.part_mm, b.flags);
-    } else {
+    else
         // tc: S3_F64 or S3_DF64 (FP64 vectors either way; the CCSS layout runs FP64)
         s = g->opt.layout == S3_LAYOUT_CCSS && g->has_ccss ? run_ccss(g, S3_F64, b.x64, b.z64, 1, b.flags, st)
                                                             : run_edges(g, tc, b.x64, b.z64, 1, b.flags, st);
-        if (s != S3_OK) return s;
-        nqz_ratio_kernel<double><<<kNqzBlocks, kNqzThreads, 0, st>>>(b.z64, b.x64, n, k, b.part_mm, b.flags);
+    if (s != S3_OK) return s;
+    return nqz_after(g, b, tc == S3_F32 ? S3_F32 : S3_F64, false, tol, max_iter, st);
+}
+
+// ------------------------------------------ one NQZ update from a whole z --
+//
+// For callers that assemble z = B xhat^(N-1) themselves (e.g. the sum of the
+// partial results of edge shards on several GPUs): the bracket of Algorithm 1
+// from z and xhat, and the next iterate r = z^(1/(N-1)) both with 1-norm 1 and
+// rescaled to max 1 (the ratio z / xhat^(N-1) does not depend on the scale of
+// xhat, so the S^3TTVc input can be kept at max 1 and z in range).
+
+enum { US_LO = 0, US_HI = 1, US_SUM = 2, US_MAX = 3 };
+
+__global__ void __launch_bounds__(kNqzThreads) nqz_update_kernel(const double *__restrict__ z,
+                                                                 const double *__restrict__ xhat, int64_t n, int k,
+                                                                 double *__restrict__ r, double *__restrict__ part,
+                                                                 double *__restrict__ scal, int32_t *flags) {
+    __shared__ double sa[kNqzThreads / 32], sb[kNqzThreads / 32];
+    __shared__ int last;
+    double acc = 0.0, mx = 0.0, lo = INFINITY, hi = -INFINITY;
+    for (int64_t v = (int64_t)blockIdx.x * kNqzThreads + threadIdx.x; v < n; v += (int64_t)gridDim.x * kNqzThreads) {
+        const double zv = z[v];
+        double pk = 1.0, base = xhat[v];
+        for (int q = k; q > 0; q >>= 1) {
+            if (q & 1) pk *= base;
+            base *= base;
+        }
+        const double ratio = zv / pk;
+        lo = fmin(lo, ratio);
+        hi = fmax(hi, ratio);
+        const double rv = root_k(zv, k);
+        r[v] = rv;
+        acc += rv;
+        mx = fmax(mx, rv);
     }
+    const double bsum = block_sum(acc, sa);
+    block_minmax(lo, hi, sa, sb);
+    double dummy = 0.0;
+    block_minmax(dummy, mx, sa, sb);
+    if (threadIdx.x == 0) {
+        part[4 * blockIdx.x] = bsum;
+        part[4 * blockIdx.x + 1] = lo;
+        part[4 * blockIdx.x + 2] = hi;
+        part[4 * blockIdx.x + 3] = mx;
+        __threadfence();
+        last = atomicAdd(flags + F_COUNT, 1) == (int)gridDim.x - 1;
+    }
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    acc = 0.0;
+    mx = 0.0;
+    lo = INFINITY;
+    hi = -INFINITY;
+    for (int i = threadIdx.x; i < (int)gridDim.x; i += kNqzThreads) {
+        acc += __ldcg(part + 4 * i);
+        lo = fmin(lo, __ldcg(part + 4 * i + 1));
+        hi = fmax(hi, __ldcg(part + 4 * i + 2));
+        mx = fmax(mx, __ldcg(part + 4 * i + 3));
+    }
+    const double tot = block_sum(acc, sa);
+    block_minmax(lo, hi, sa, sb);
+    dummy = 0.0;
+    block_minmax(dummy, mx, sa, sb);
+    if (threadIdx.x == 0) {
+        scal[US_LO] = lo;
+        scal[US_HI] = hi;
+        scal[US_SUM] = tot;
+        scal[US_MAX] = mx;
+        flags[F_COUNT] = 0;
+    }
+}
+
+__global__ void __launch_bounds__(kNqzThreads) nqz_update_scale_kernel(const double *__restrict__ r, int64_t n,
+                                                                       const double *__restrict__ scal,
+                                                                       double *__restrict__ x1,
+                                                                       double *__restrict__ xmax) {
+    const double inv_sum = 1.0 / scal[US_SUM], inv_max = 1.0 / scal[US_MAX];
+    for (int64_t v = (int64_t)blockIdx.x * kNqzThreads + threadIdx.x; v < n; v += (int64_t)gridDim.x * kNqzThreads) {
+        const double rv = r[v];
+        x1[v] = rv * inv_sum;
+        xmax[v] = rv * inv_max;
+    }
+}
+
+// ------------------------------------------------ Z-eigenpairs (SS-HOPM) --
+//
+// The shifted power method for the order-N blowup tensor (Sec. I names it and
+// symmetric CP as consumers of S^3TTVc): x <- (B x^(N-1) + alpha x)/||.||_2,
+// lambda = x . B x^(N-1).  S^3TTVc runs on xhat = x / m (m = max |x|, so xhat
+// has entries <= 1 at any rank); with zhat = B xhat^(N-1) = B x^(N-1) / m^(N-1)
+//     w = zhat - sum_q c_q x_q + sigma x,   sigma = alpha m^-(N-1),
+//     c_q = lambda_q (x_q . xhat)^(N-1)     (greedy CP: the deflated components),
+//     lambda = m^(N-1) x . (zhat - sum_q c_q x_q),
+// and w is a positive multiple of the true shifted product.
+
+constexpr int kZeigMaxR = 32;
+// scalars: sigma, ||w||_2, x . zd, max |w|, m; deflation coefficients c_q and lambda_q
+enum { ZS_SIGMA = 1, ZS_NORM = 2, ZS_DOT = 3, ZS_MAX = 4, ZS_M = 5, ZS_C = 8, ZS_LAM = 8 + kZeigMaxR,
+       ZS_LEN = 8 + 2 * kZeigMaxR };
+
+// d_q = X_q . xhat for q < R (X: R rows of n), then c_q = lambda_q d_q^k in the last block.
+__global__ void __launch_bounds__(kNqzThreads) zeig_dots_kernel(const double *__restrict__ X, int R,
+                                                                const double *__restrict__ xhat, int64_t n, int k,
+                                                                double *__restrict__ part, double *__restrict__ scal,
+                                                                int32_t *flags) {
+    __shared__ double sa[kNqzThreads / 32];
+    __shared__ int last;
+    for (int q = 0; q < R; ++q) {
+        double acc = 0.0;
+        for (int64_t v = (int64_t)blockIdx.x * kNqzThreads + threadIdx.x; v < n; v += (int64_t)gridDim.x * kNqzThreads)
+            acc += X[(int64_t)q * n + v] * xhat[v];
+        const double b = block_sum(acc, sa);
+        if (threadIdx.x == 0) part[(int64_t)q * gridDim.x + blockIdx.x] = b;
+    }
+    if (threadIdx.x == 0) {
+        __threadfence();
+        last = atomicAdd(flags + F_COUNT, 1) == (int)gridDim.x - 1;
+    }
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    for (int q = 0; q < R; ++q) {
+        double acc = 0.0;
+        for (int i = threadIdx.x; i < (int)gridDim.x; i += kNqzThreads) acc += __ldcg(part + (int64_t)q * gridDim.x + i);
+        const double d = block_sum(acc, sa);
+        if (threadIdx.x == 0) {
+            double p = 1.0, base = d;
+            for (int e = k; e > 0; e >>= 1) {
+                if (e & 1) p *= base;
+                base *= base;
+            }
+            scal[ZS_C + q] = scal[ZS_LAM + q] * p;
+        }
+    }
+    if (threadIdx.x == 0) flags[F_COUNT] = 0;
+}
+
+// w = zhat - sum_q c_q X_q + sigma x; ||w||_2, x . (zhat - sum_q c_q X_q) and max |w| to scal.
+__global__ void __launch_bounds__(kNqzThreads) zeig_update_kernel(const double *__restrict__ zhat,
+                                                                  const double *__restrict__ x,
+                                                                  const double *__restrict__ X, int R, int use_sigma,
+                                                                  int64_t n, double *__restrict__ w,
+                                                                  double *__restrict__ part, double *__restrict__ scal,
+                                                                  int32_t *flags) {
+    __shared__ double sa[kNqzThreads / 32], sb[kNqzThreads / 32];
+    __shared__ double c[kZeigMaxR];
+    __shared__ int last;
+    if (threadIdx.x < R) c[threadIdx.x] = scal[ZS_C + threadIdx.x];
+    __syncthreads();
+    const double sigma = use_sigma ? scal[ZS_SIGMA] : 0.0;
+    double s2 = 0.0, dot = 0.0, mx = 0.0;
+    for (int64_t v = (int64_t)blockIdx.x * kNqzThreads + threadIdx.x; v < n; v += (int64_t)gridDim.x * kNqzThreads) {
+        double zd = zhat[v];
+        for (int q = 0; q < R; ++q) zd -= c[q] * X[(int64_t)q * n + v];
+        const double xv = x[v];
+        const double wv = fma(sigma, xv, zd);
+        w[v] = wv;
+        s2 = fma(wv, wv, s2);
+        dot = fma(xv, zd, dot);
+        mx = fmax(mx, fabs(wv));
+    }
+    const double b2 = block_sum(s2, sa);
+    const double bd = block_sum(dot, sa);
+    double lo = 0.0;
+    block_minmax(lo, mx, sa, sb);
+    if (threadIdx.x == 0) {
+        part[3 * blockIdx.x] = b2;
+        part[3 * blockIdx.x + 1] = bd;
+        part[3 * blockIdx.x + 2] = mx;
+        __threadfence();
+        last = atomicAdd(flags + F_COUNT, 1) == (int)gridDim.x - 1;
+    }
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    s2 = 0.0;
+    dot = 0.0;
+    mx = 0.0;
+    for (int i = threadIdx.x; i < (int)gridDim.x; i += kNqzThreads) {
+        s2 += __ldcg(part + 3 * i);
+        dot += __ldcg(part + 3 * i + 1);
+        mx = fmax(mx, __ldcg(part + 3 * i + 2));
+    }
+    const double t2 = block_sum(s2, sa);
+    const double td = block_sum(dot, sa);
+    lo = 0.0;
+    block_minmax(lo, mx, sa, sb);
+    if (threadIdx.x == 0) {
+        scal[ZS_NORM] = sqrt(t2);
+        scal[ZS_DOT] = td;
+        scal[ZS_MAX] = mx;
+        flags[F_COUNT] = 0;
+    }
+}
+
+// x = w / ||w||_2, xhat = w / max |w|; m = max |x| and sigma = alpha m^-k for the next step.
+__global__ void __launch_bounds__(kNqzThreads) zeig_normalize_kernel(const double *__restrict__ w, int64_t n,
+                                                                     double *__restrict__ x, double *__restrict__ xhat,
+                                                                     double *__restrict__ scal, double alpha, int k) {
+    const double inv_norm = 1.0 / scal[ZS_NORM], inv_max = 1.0 / scal[ZS_MAX];
+    for (int64_t v = (int64_t)blockIdx.x * kNqzThreads + threadIdx.x; v < n; v += (int64_t)gridDim.x * kNqzThreads) {
+        x[v] = w[v] * inv_norm;
+        xhat[v] = w[v] * inv_max;
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        const double m = scal[ZS_MAX] * inv_norm;
+        double p = 1.0, base = 1.0 / m;
+        for (int e = k; e > 0; e >>= 1) {
+            if (e & 1) p *= base;
+            base *= base;
+        }
+        scal[ZS_M] = m;
+        scal[ZS_SIGMA] = fmin(alpha * p, 1e300);
+    }
+}
+
+s3_status ensure_zeig_scratch(s3_graph_s *g) {
+    s3_status st = ensure_nqz_scratch(g, 2);
+    if (st != S3_OK) return st;
+    if (!g->d_zeig) {
+        if ((st = dev_alloc(g, &g->d_zeig, (size_t)(kZeigMaxR + 3) * kNqzBlocks + ZS_LEN)) != S3_OK) return st;
+    }
+    return S3_OK;
+}
+
+// One SS-HOPM run on B minus the R components in X (device rows) with eigenvalues lam[R]
+// (host); x0 (device) or NULL = uniform start; result in x_out (device).
+s3_status zeig_run(s3_graph_s *g, const s3_zeig_options &opt, const double *x0, const double *X, int R,
+                   const double *lam, double *x_out, s3_zeig_result *res, cudaStream_t st) {
+    s3_status s = ensure_zeig_scratch(g);
+    if (s != S3_OK) return s;
+    const int64_t n = g->n;
+    const int k = g->N - 1;
+    double *x = g->d_nqz, *w = g->d_nqz + n, *zhat = g->d_nqz + 2 * n, *xhat = g->d_nqz + 3 * n;
+    double *part = g->d_zeig, *scal = g->d_zeig + (size_t)(kZeigMaxR + 3) * kNqzBlocks;
+    int32_t *flags = g->d_flags;
+    const unsigned gb = (unsigned)((n + 255) / 256);
+    S3_CUDA(cudaMemsetAsync(flags, 0, 8 * sizeof(int32_t), st));
+    S3_CUDA(cudaMemsetAsync(scal, 0, sizeof(double) * ZS_LEN, st));
+    if (R > 0) {
+        double h[kZeigMaxR];
+        for (int q = 0; q < R; ++q) h[q] = lam[q];
+        S3_CUDA(cudaMemcpyAsync(scal + ZS_LAM, h, sizeof(double) * R, cudaMemcpyHostToDevice, st));
+        S3_CUDA(cudaStreamSynchronize(st));   // h lives on this stack frame
+    }
+    // start: normalise x0 (or the all-ones vector) through the update/normalise pair
+    if (x0) S3_CUDA(cudaMemcpyAsync(zhat, x0, sizeof(double) * n, cudaMemcpyDeviceToDevice, st));
+    else fill_kernel<double><<<gb, 256, 0, st>>>(zhat, n, 1.0);
+    zeig_update_kernel<<<kNqzBlocks, kNqzThreads, 0, st>>>(zhat, zhat, X, 0, 0, n, w, part, scal, flags);
+    zeig_normalize_kernel<<<kNqzBlocks, kNqzThreads, 0, st>>>(w, n, x, xhat, scal, opt.alpha, k);
     S3_CUDA(cudaGetLastError());
-    nqz_check_kernel<<<1, 32, 0, st>>>(b.part_mm, kNqzBlocks, tol, max_iter, g->d_hist, g->hist_cap, b.flags);
-    S3_CUDA(cudaGetLastError());
+    double hs[8];
+    double lam_prev = 0.0, lam_cur = 0.0;
+    int it = 0;
+    res->converged = 0;
+    for (;; ++it) {
+        if (R > 0) zeig_dots_kernel<<<kNqzBlocks, kNqzThreads, 0, st>>>(X, R, xhat, n, k, part + 3 * kNqzBlocks, scal, flags);
+        S3_CUDA(cudaGetLastError());
+        s = run_edges(g, S3_F64, xhat, zhat, 0, nullptr, st);
+        if (s != S3_OK) return s;
+        zeig_update_kernel<<<kNqzBlocks, kNqzThreads, 0, st>>>(zhat, x, X, R, 1, n, w, part, scal, flags);
+        S3_CUDA(cudaGetLastError());
+        S3_CUDA(cudaMemcpyAsync(hs, scal, sizeof(hs), cudaMemcpyDeviceToHost, st));
+        S3_CUDA(cudaStreamSynchronize(st));
+        lam_cur = std::pow(hs[ZS_M], (double)k) * hs[ZS_DOT];
+        if (!std::isfinite(lam_cur) || !(hs[ZS_NORM] > 0.0)) return fail(S3_ERANGE, "Z-eigenvalue left the FP64 range");
+        if (it > 0 && std::fabs(lam_cur - lam_prev) < opt.tol * std::max(1.0, std::fabs(lam_cur))) {
+            res->converged = 1;
+            break;
+        }
+        if (it >= opt.max_iter) break;
+        zeig_normalize_kernel<<<kNqzBlocks, kNqzThreads, 0, st>>>(w, n, x, xhat, scal, opt.alpha, k);
+        S3_CUDA(cudaGetLastError());
+        lam_prev = lam_cur;
+    }
+    res->lambda = lam_cur;
+    res->iters = it;
+    S3_CUDA(cudaMemcpyAsync(x_out, x, sizeof(double) * n, cudaMemcpyDeviceToDevice, st));
     return S3_OK;
 }
 
@@ -301,6 +604,7 @@ s3_status s3_hcentrality(s3_graph_t g, const s3_nqz_options *opt_in, const doubl
     b.z32 = g->d_z32;
     b.part_sum = g->d_red;
     b.part_mm = g->d_red + kNqzBlocks;
+    b.scal = g->d_red + 3 * kNqzBlocks;
     b.flags = g->d_flags;
     const int64_t n = g->n;
     const unsigned gb = (unsigned)((n + 255) / 256);
@@ -326,6 +630,9 @@ s3_status s3_hcentrality(s3_graph_t g, const s3_nqz_options *opt_in, const doubl
     };
     s = ttsv(phase);
     if (s != S3_OK) return s;
+    // the first root vector (no bracket yet: Algorithm 1 tests only after the loop's S^3TTVc)
+    s = nqz_after(g, b, phase == S3_F32 ? S3_F32 : S3_F64, true, opt.tol, opt.max_iter, st);
+    if (s != S3_OK) return s;
 
     int32_t flags[8] = {0};
     std::vector<double> hist;
@@ -337,7 +644,7 @@ s3_status s3_hcentrality(s3_graph_t g, const s3_nqz_options *opt_in, const doubl
         const double tol = phase == S3_F32 ? std::max(opt.switch_tol, opt.tol) : opt.tol;
         // a graph of check_every passes (the first pass after a precision change runs eagerly)
         if (last_z != phase) {
-            s = nqz_step(g, b, last_z, phase, tol, opt.max_iter, st);
+            s = nqz_step(g, b, phase, tol, opt.max_iter, st);
             if (s != S3_OK) return s;
             last_z = phase;
         } else {
@@ -354,7 +661,7 @@ s3_status s3_hcentrality(s3_graph_t g, const s3_nqz_options *opt_in, const doubl
                 S3_CUDA(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
                 s3_status cs = S3_OK;
                 for (int i = 0; i < opt.check_every && cs == S3_OK; ++i)
-                    cs = nqz_step(g, b, phase, phase, tol, opt.max_iter, st);
+                    cs = nqz_step(g, b, phase, tol, opt.max_iter, st);
                 cudaError_t ce = cudaStreamEndCapture(st, &graph);
                 if (cs != S3_OK) {
                     if (graph) cudaGraphDestroy(graph);
@@ -399,8 +706,11 @@ s3_status s3_hcentrality(s3_graph_t g, const s3_nqz_options *opt_in, const doubl
                 phase = hi;
                 switched = true;
                 if (flags[F_RANGE]) {
-                    // the last FP32 z is unusable: redo z = TTSV1(x) in FP64 from the same x
+                    // the last FP32 z is unusable: redo z = TTSV1(x) in FP64 from the same x,
+                    // and the root vector from it
                     s = ttsv(hi);
+                    if (s != S3_OK) return s;
+                    s = nqz_after(g, b, S3_F64, true, opt.tol, opt.max_iter, st);
                     if (s != S3_OK) return s;
                     last_z = hi;
                 }
@@ -430,6 +740,99 @@ s3_status s3_hcentrality(s3_graph_t g, const s3_nqz_options *opt_in, const doubl
     res->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
     if (flags[F_RANGE] && !res->converged) return fail(S3_ERANGE, "ratio z/x^(N-1) left the FP64 range");
     if (!res->converged) return fail(S3_ENOCONV, "NQZ did not reach the tolerance within max_iter");
+    return S3_OK;
+}
+
+s3_status s3_nqz_update(s3_graph_t g, const double *z, const double *xhat, double *x_next, double *xhat_next,
+                        double *lambda, void *stream) {
+    if (!g || !z || !xhat || !x_next || !xhat_next || !lambda) return fail(S3_EINVAL, "NULL argument");
+    if (g->N < 2) return fail(S3_EINVAL, "NQZ needs rank >= 2");
+    if (x_next == xhat_next) return fail(S3_EINVAL, "x_next and xhat_next must differ");
+    DeviceGuard guard(g->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    s3_status s = ensure_zeig_scratch(g);
+    if (s != S3_OK) return s;
+    double *part = g->d_zeig, *scal = g->d_zeig + (size_t)(kZeigMaxR + 3) * kNqzBlocks;
+    S3_CUDA(cudaMemsetAsync(g->d_flags + F_COUNT, 0, sizeof(int32_t), st));
+    nqz_update_kernel<<<kNqzBlocks, kNqzThreads, 0, st>>>(z, xhat, g->n, g->N - 1, x_next, part, scal, g->d_flags);
+    nqz_update_scale_kernel<<<kNqzBlocks, kNqzThreads, 0, st>>>(x_next, g->n, scal, x_next, xhat_next);
+    S3_CUDA(cudaGetLastError());
+    double h[4];
+    S3_CUDA(cudaMemcpyAsync(h, scal, sizeof(h), cudaMemcpyDeviceToHost, st));
+    s = mark_done(g, st);
+    if (s != S3_OK) return s;
+    S3_CUDA(cudaStreamSynchronize(st));
+    lambda[0] = h[US_LO];
+    lambda[1] = h[US_HI];
+    if (!(h[US_LO] > 0.0) || !std::isfinite(h[US_HI]) || !(h[US_SUM] > 0.0))
+        return fail(S3_ERANGE, "NQZ ratios or roots left the FP64 range (a node with z = 0 or x = 0?)");
+    return S3_OK;
+}
+
+s3_status s3_zeig_options_init(s3_zeig_options *opt) {
+    if (!opt) return fail(S3_EINVAL, "opt is NULL");
+    std::memset(opt, 0, sizeof(*opt));
+    opt->alpha = 0.0;
+    opt->tol = 1e-12;
+    opt->max_iter = 10000;
+    return S3_OK;
+}
+
+namespace {
+s3_status zeig_check(s3_graph_t g, const s3_zeig_options *opt_in, s3_zeig_options &opt) {
+    if (!g) return fail(S3_EINVAL, "graph is NULL");
+    if (opt_in) opt = *opt_in;
+    else s3_zeig_options_init(&opt);
+    if (opt.max_iter <= 0) opt.max_iter = 10000;
+    if (!(opt.tol > 0)) return fail(S3_EINVAL, "tol must be > 0");
+    if (!(opt.alpha >= 0)) return fail(S3_EINVAL, "alpha must be >= 0");
+    if (g->N < 2) return fail(S3_EINVAL, "Z-eigenpairs need rank >= 2");
+    return S3_OK;
+}
+}  // namespace
+
+s3_status s3_zeigenpair(s3_graph_t g, const s3_zeig_options *opt_in, const double *x0, double *x_out,
+                        s3_zeig_result *res, void *stream) {
+    auto t0 = std::chrono::steady_clock::now();
+    s3_zeig_options opt;
+    s3_status s = zeig_check(g, opt_in, opt);
+    if (s != S3_OK) return s;
+    if (!x_out || !res) return fail(S3_EINVAL, "NULL argument");
+    std::memset(res, 0, sizeof(*res));
+    DeviceGuard guard(g->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    s = zeig_run(g, opt, x0, nullptr, 0, nullptr, x_out, res, st);
+    if (s != S3_OK) return s;
+    s = mark_done(g, st);
+    if (s != S3_OK) return s;
+    S3_CUDA(cudaStreamSynchronize(st));
+    res->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    if (!res->converged) return fail(S3_ENOCONV, "SS-HOPM did not reach the tolerance within max_iter");
+    return S3_OK;
+}
+
+s3_status s3_symmetric_cp(s3_graph_t g, int32_t R, const s3_zeig_options *opt_in, const double *X0, double *X,
+                          double *lambdas, int32_t *iters, void *stream) {
+    s3_zeig_options opt;
+    s3_status s = zeig_check(g, opt_in, opt);
+    if (s != S3_OK) return s;
+    if (R < 1 || R > kZeigMaxR) return fail(S3_EINVAL, "R must be in 1..32");
+    if (!X || !lambdas) return fail(S3_EINVAL, "NULL argument");
+    DeviceGuard guard(g->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    bool all = true;
+    for (int r = 0; r < R; ++r) {
+        s3_zeig_result res{};
+        s = zeig_run(g, opt, X0 ? X0 + (int64_t)r * g->n : nullptr, X, r, lambdas, X + (int64_t)r * g->n, &res, st);
+        if (s != S3_OK) return s;
+        lambdas[r] = res.lambda;
+        if (iters) iters[r] = res.iters;
+        all = all && res.converged;
+    }
+    s = mark_done(g, st);
+    if (s != S3_OK) return s;
+    S3_CUDA(cudaStreamSynchronize(st));
+    if (!all) return fail(S3_ENOCONV, "a component did not reach the tolerance within max_iter");
     return S3_OK;
 }
 

@@ -819,10 +819,6 @@ __device__ __forceinline__ void warp_edge_compute(const EdgeBucketArgs &b, const
     __syncwarp();
 }
 
-// Elements of T per warp for warp_edge_compute.
-__host__ __device__ constexpr int64_t warp_smem_elems(int s, int W) {
-    return ((2 * (int64_t)s + (int64_t)(s > 2 ? s - 2 : 0) * W + 4 * (int64_t)W) + 3) / 4 * 4;
-}
 
 // One edge per warp, grid-stride over the bucket.
 template <typename T>

@@ -1,0 +1,159 @@
+"""The Bernoulli form of the leave-one-out, checked on the CPU.
+
+The Bernoulli kernels evaluate, for an edge e of size s at rank N (W = N-s+1),
+    c(e, v_i) / K(s,N) = (prod_{j != i} x_j) * sum_{k<W} G[W-1-k] beta_k x_i^k,
+with G = prod_j g_{x_j} truncated to W coefficients, g_x(t) = (e^(x t) - 1)/(x t),
+and beta_k = B_k^+ / k! the coefficients of z / (1 - e^(-z)).  That rests on
+E(x t) / Ebar(x t) = 1 / (1 - e^(-x t)) (Sec. II-A's E and Ebar).  These tests
+  * check beta_k against the Bernoulli numbers B_k (exact rationals, from their
+    defining recurrence),
+  * check the identity in exact rationals against the oracle's generating-function
+    value of Algorithm 2, for edges of every size at several ranks, zeros included,
+  * replay the kernels' FP32 operation order in numpy float32 (the same Horner
+    forms, the x^4-Horner split of the sum into its positive part P and negative
+    part Q, prefix and suffix products) and check that every member the gate
+    (P + Q <= 4 (P - Q)) accepts is within the FP32 tolerance of the exact value,
+    and that the gate rejects the badly conditioned edges.
+The GPU tests check the kernels themselves against the oracle.
+"""
+from fractions import Fraction
+from math import comb, factorial
+
+import numpy as np
+import pytest
+
+from oracle import exact
+
+F = np.float32
+
+
+def bernoulli_plus(n):
+    """B_0..B_n with B_1 = +1/2, from sum_{j<=m} C(m+1, j) B_j = 0 (B_1 = -1/2 convention)."""
+    B = [Fraction(1)]
+    for m in range(1, n + 1):
+        B.append(-sum(comb(m + 1, j) * B[j] for j in range(m)) / (m + 1))
+    B[1] = -B[1]
+    return B
+
+
+def beta_exact(n):
+    return [b / factorial(k) for k, b in enumerate(bernoulli_plus(n))]
+
+
+def test_beta_is_the_series_of_z_over_one_minus_exp():
+    # z / (1 - e^-z) * (1 - e^-z) / z = 1: the Cauchy product of beta with
+    # f_k = (-1)^k / (k+1)! is 1, 0, 0, ...
+    beta = beta_exact(31)
+    f = [Fraction((-1) ** k, factorial(k + 1)) for k in range(32)]
+    for m in range(32):
+        assert sum(beta[k] * f[m - k] for k in range(m + 1)) == (1 if m == 0 else 0)
+    assert beta[:5] == [1, Fraction(1, 2), Fraction(1, 12), 0, Fraction(-1, 720)]
+    assert all(beta[k] == 0 for k in range(3, 32, 2))
+
+
+def bern_exact(xs, i, N):
+    s = len(xs)
+    W = N - s + 1
+    beta = beta_exact(max(W - 1, 1))
+    G = [Fraction(1)] + [Fraction(0)] * (W - 1)
+    for xj in xs:
+        g = [Fraction(xj) ** k / factorial(k + 1) for k in range(W)]
+        G = [sum(G[m - k] * g[k] for k in range(m + 1)) for m in range(W)]
+    prod = Fraction(1)
+    for j, xj in enumerate(xs):
+        if j != i:
+            prod *= Fraction(xj)
+    return prod * sum(G[W - 1 - k] * beta[k] * Fraction(xs[i]) ** k for k in range(W))
+
+
+@pytest.mark.parametrize("N", [6, 9, 13])
+def test_identity_matches_algorithm2_exactly(N):
+    rng = np.random.default_rng(N)
+    for s in range(2, N + 1):
+        for trial in range(2):
+            xs = [Fraction(int(v), 8) for v in rng.integers(0, 17, size=s)]
+            if trial == 1:
+                xs[0] = Fraction(0)           # a zero member
+            edge = tuple(range(s))
+            for i in range(s):
+                # Algorithm 2's per-pair value divided by its scale K(s,N)
+                want = exact.contribution_gf(edge, i, {v: xs[v] for v in edge}, N) / exact.edge_scale(N, s)
+                assert bern_exact(xs, i, N) == want, (N, s, i)
+
+
+def bern_fp32(a, W):
+    """(values, P, Q) per member in the kernels' FP32 order; a: the already scaled x."""
+    s = len(a)
+    beta = [F(float(b)) for b in beta_exact(max(W - 1, 1))]
+    x0 = a[0]
+    G = [F(1)] + [F(0)] * (W - 1)
+    for k in range(1, W):
+        G[k] = F(G[k - 1] * F(x0 * F(1.0 / (k + 1))))
+    pre = [F(1)] * s
+    prod = x0
+    for i in range(1, s):
+        xi = a[i]
+        pre[i] = prod
+        prod = F(prod * xi)
+        r = [F(0)] + [F(xi * F(1.0 / (k + 1))) for k in range(1, W)]
+        for m in range(W - 1, 0, -1):
+            t = G[0]
+            for j in range(1, m + 1):
+                t = F(np.float32(np.float64(r[m - j + 1]) * np.float64(t) + np.float64(G[j])))  # one rounding
+            G[m] = t
+    H = [F(G[W - 1 - k] * beta[k]) for k in range(W)]
+    fma = lambda a_, b_, c_: F(np.float64(a_) * np.float64(b_) + np.float64(c_))
+    vals, Ps, Qs = [F(0)] * s, [F(0)] * s, [F(0)] * s
+    suf = F(1)
+    for i in range(s - 1, -1, -1):
+        xi = a[i]
+        x2 = F(xi * xi)
+        x4 = F(x2 * x2)
+        p2 = F(0)
+        if W > 2:
+            for k in range(2 + 4 * ((W - 3) // 4), 1, -4):
+                p2 = fma(p2, x4, H[k])
+        p = H[0]
+        if W > 1:
+            p = fma(H[1], xi, p)
+        P = fma(p2, x2, p)
+        q = F(0)
+        if W > 4:
+            for k in range(4 + 4 * ((W - 5) // 4), 3, -4):
+                q = fma(q, x4, F(-H[k]))
+            q = F(q * x4)
+        vals[i] = F(F(P - q) * F(pre[i] * suf))
+        Ps[i], Qs[i] = P, q
+        suf = F(suf * xi)
+    return vals, Ps, Qs
+
+
+@pytest.mark.parametrize("N", [12, 25])
+def test_fp32_replay_within_tolerance_when_the_gate_accepts(N):
+    rng = np.random.default_rng(7 + N)
+    accepted = rejected = 0
+    for s in range(6, N + 1):
+        W = N - s + 1
+        for spread in (1.2, 2.0, 4.0, 16.0):
+            # x near 1 / s (the kernels scale each edge by a power of two), members up to
+            # `spread` times apart
+            raw = rng.uniform(1.0, spread, size=s) / s
+            a = [F(v) for v in raw]
+            vals, P, Q = bern_fp32(a, W)
+            ok = all(float(P[i] + Q[i]) <= 4.0 * float(P[i] - Q[i]) for i in range(s))
+            if not ok:
+                rejected += 1
+                continue
+            accepted += 1
+            for i in range(s):
+                want = bern_exact([Fraction(float(v)) for v in a], i, N)
+                err = abs(Fraction(float(vals[i])) - want) / want
+                assert err <= Fraction(1, 10 ** 5), (N, s, spread, i, float(err))
+    assert accepted > 0
+
+
+def test_gate_rejects_badly_conditioned_edges():
+    # one member 40 times the others at s = 6, N = 25: the alternating sum cancels
+    a = [F(0.02)] * 5 + [F(0.8)]
+    vals, P, Q = bern_fp32(a, 20)
+    assert any(float(P[i] + Q[i]) > 4.0 * float(P[i] - Q[i]) for i in range(6))
