@@ -49,7 +49,10 @@ int size_bin(int s, int N) {
     return b < 0 ? 0 : (b > 7 ? 7 : b);
 }
 
-// one thread per edge of one bucket
+// One thread per edge of one bucket.  Members of neighbouring edges are often the
+// same node (edges are sorted, hubs first), so the lanes of a warp that target one
+// node combine their updates and one lane issues the atomics (the integer sums are
+// exact in any order).
 __global__ void feature_edge_kernel(EdgeBucketArgs b, int bin, const int64_t *__restrict__ inc_ptr,
                                     unsigned long long *__restrict__ nbr, unsigned int *__restrict__ size_sum,
                                     int *__restrict__ size_max, unsigned int *__restrict__ hist) {
@@ -61,13 +64,21 @@ __global__ void feature_edge_kernel(EdgeBucketArgs b, int bin, const int64_t *__
         int v = b.ids[(int64_t)i * b.ld + e];
         D += (unsigned long long)(inc_ptr[v + 1] - inc_ptr[v]);
     }
+    const unsigned act = __activemask();
+    const int lane = threadIdx.x & 31;
     for (int i = 0; i < s; ++i) {
-        int v = b.ids[(int64_t)i * b.ld + e];
-        unsigned long long dv = (unsigned long long)(inc_ptr[v + 1] - inc_ptr[v]);
-        atomicAdd(nbr + v, D - dv);
-        atomicAdd(size_sum + v, (unsigned int)s);
-        atomicMax(size_max + v, s);
-        atomicAdd(hist + (int64_t)v * 8 + bin, 1u);
+        const int v = b.ids[(int64_t)i * b.ld + e];
+        const unsigned long long dv = (unsigned long long)(inc_ptr[v + 1] - inc_ptr[v]);
+        const unsigned grp = __match_any_sync(act, v);
+        unsigned long long acc = 0;
+        for (unsigned mm = grp; mm; mm &= mm - 1) acc += __shfl_sync(grp, D - dv, __ffs(mm) - 1);
+        if (lane == __ffs(grp) - 1) {
+            const unsigned cnt = (unsigned)__popc(grp);
+            atomicAdd(nbr + v, acc);
+            atomicAdd(size_sum + v, cnt * (unsigned int)s);
+            atomicMax(size_max + v, s);
+            atomicAdd(hist + (int64_t)v * 8 + bin, cnt);
+        }
     }
 }
 

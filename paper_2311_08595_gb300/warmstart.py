@@ -87,13 +87,42 @@ def evaluate(hg, model, tol=1e-8, precision=0):
             "speedup": tu / tw, "max_rel_diff_x": diff}
 
 
+def start_cost(hg, model, reps=5):
+    """Device time of the warm start alone (features, MLP, exponentiation and normalisation)
+    on hg, in ms, against one FP32 and one FP64 S^3TTVc call on the same handle."""
+    import torch
+
+    from . import s3_sttsvc, s3_warmstart
+    g = s3_build_format(hg.n, hg.edge_ptr, hg.members)
+    s3_warmstart(g, model)
+    x32 = torch.ones(hg.n, dtype=torch.float32, device="cuda")
+    y32 = torch.empty_like(x32)
+    x64, y64 = x32.double(), torch.empty(hg.n, dtype=torch.float64, device="cuda")
+    st = torch.cuda.current_stream()
+    out = {}
+    for name, fn in (("warm_start_ms", lambda: s3_warmstart(g, model)), ("sttsvc_f32_ms", lambda: s3_sttsvc(g, x32, y32)),
+                     ("sttsvc_f64_ms", lambda: s3_sttsvc(g, x64, y64))):
+        fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        for _ in range(reps):
+            fn()
+        e1.record(st)
+        torch.cuda.synchronize()
+        out[name] = e0.elapsed_time(e1) / reps
+    s3_destroy(g)
+    return out
+
+
 def main():
     import s3synth
     ap = argparse.ArgumentParser()
     ap.add_argument("--graphs", type=int, default=500)
     ap.add_argument("--n", type=int, default=50000)
     ap.add_argument("--epochs", type=int, default=4)
-    ap.add_argument("--out", default="warmstart_weights.npy")
+    ap.add_argument("--out", default="warmstart_weights.npy",
+                    help="the package ships paper_2311_08595_gb300/data/warmstart_500x50k.npy, made with the defaults")
     a = ap.parse_args()
     rng = np.random.default_rng(12345)
     hgs = [s3synth.largest_component(s3synth.config_powerlaw(n=a.n, m=5 * a.n, seed=int(rng.integers(1 << 30))))[0]

@@ -70,3 +70,21 @@ def test_training_reduces_loss_and_warm_start_helps():
     assert r["learned"]["iters"] <= r["uniform"]["iters"]
     x0 = s3.s3_warmstart(s3.s3_build_format(held.n, held.edge_ptr, held.members), model)
     assert torch.all(x0 > 0) and abs(float(x0.sum()) - 1.0) < 1e-12
+
+
+def test_shipped_network_saves_iterations_on_held_out_graph():
+    # the network the package ships (500 training hypergraphs of n = 50k, power-law recipe)
+    # on a held-out hypergraph of the same recipe and another size: strictly fewer NQZ
+    # iterations to 1e-8 than the uniform start, and the same centrality
+    import os
+
+    import paper_2311_08595_gb300 as s3
+    from paper_2311_08595_gb300 import warmstart as ws
+    path = os.path.join(os.path.dirname(s3.__file__), "data", "warmstart_500x50k.npy")
+    model = s3.s3_mlp_create(params=np.load(path))
+    held = s3synth.largest_component(s3synth.config_powerlaw(n=200000, m=1000000, rank=25, seed=777))[0]
+    for prec in (0, 3):
+        r = ws.evaluate(held, model, tol=1e-8, precision=prec)
+        print("shipped warm start, precision", prec, r)
+        assert r["learned"]["iters"] < r["uniform"]["iters"], r
+        assert r["max_rel_diff_x"] < 1e-7
