@@ -155,19 +155,26 @@ constexpr double kBernKmax32 = 4.0, kBernKmax64 = 64.0;
 }
 
 // Which call types evaluate bucket k in the Bernoulli form (bit 1 = FP32, 2 = FP64):
-// 6 <= s <= 64, W <= thread_max_w, not in closed form for that type, fewer multiply-adds
-// than the prefix/suffix series, and equal x amplified at most kmax / 2.
+// 6 <= s <= 64, W <= thread_max_w, not in closed form for that type, fewer operations
+// than the prefix/suffix series, and equal x with a gate ratio of at most kmax / 2 (so that
+// x of somewhat different sizes still pass).  FP32 forms G as a product of the members'
+// series, FP64 from their power sums (s3_bern.cuh); each has its own gate ratio and count.
 int bernoulli_mask(const s3_graph_s *g, size_t k, const double beta[32]) {
     if (g->opt.bernoulli < 0) return 0;
     const int tmw = (g->opt.thread_max_w <= 0 || g->opt.thread_max_w > 32) ? 32 : g->opt.thread_max_w;
     const HostBucket &hb = g->buckets[k];
     const int s = hb.s, W = g->N - s + 1;
     if (s < 6 || s > 64 || hb.m <= 0 || W < 1 || W > tmw) return 0;
+    // operations per edge: the series' products and dots; the product form's products and
+    // per-member sums; the power-sum form's power sums, both recurrences and per-member sums
     const double series = (2.0 * s - 5.0) * W * (W + 1) / 2.0 + 2.0 * s * W;
-    const double bern = (double)s * W * (W - 1) / 2.0 + 3.0 * s * W;
-    if (!(bern < 0.9 * series)) return 0;
-    // equal x: G = ((e^z - 1)/z)^s on W coefficients, kappa = sum |G[W-1-k] beta_k| / sum G[W-1-k] beta_k
-    std::vector<double> c(W), G(W, 0.0), Gn(W);
+    const double prod_form = (double)s * W * (W - 1) / 2.0 + 3.0 * s * W;
+    const double sum_form = 2.0 * s * (W - 1) + (double)W * (W - 1) + 2.0 * s * W;
+    // equal x (= 1).  Product form: G = ((e^z - 1)/z)^s on W coefficients; gate ratio
+    // sum_k |G[W-1-k] beta_k| / sum_k G[W-1-k] beta_k.  Power-sum form: the recurrence
+    // G_m = (1/m) sum_j beta_j p_j G_{m-j} with p_j = s, its majorant A (|beta_j|), and the
+    // ratio sum_k A[W-1-k] |beta_k| / sum_k G[W-1-k] beta_k.
+    std::vector<double> c(W), G(W, 0.0), Gn(W), R(W, 0.0), A(W, 0.0);
     double fact = 1.0;
     for (int i = 0; i < W; ++i) {
         fact *= (double)(i + 1);
@@ -182,16 +189,29 @@ int bernoulli_mask(const s3_graph_s *g, size_t k, const double beta[32]) {
         }
         G.swap(Gn);
     }
-    double sum = 0.0, abs_sum = 0.0;
+    R[0] = A[0] = 1.0;
+    for (int m = 1; m < W; ++m) {
+        double acc = 0.0, acca = 0.0;
+        for (int i = 1; i <= m; ++i) {
+            acc += beta[i] * s * R[m - i];
+            acca += std::fabs(beta[i]) * s * A[m - i];
+        }
+        R[m] = acc / m;
+        A[m] = acca / m;
+    }
+    double sum = 0.0, abs_sum = 0.0, rsum = 0.0, maj = 0.0;
     for (int i = 0; i < W; ++i) {
         sum += G[W - 1 - i] * beta[i];
         abs_sum += std::fabs(G[W - 1 - i] * beta[i]);
+        rsum += R[W - 1 - i] * beta[i];
+        maj += A[W - 1 - i] * std::fabs(beta[i]);
     }
-    const double kappa = sum > 0.0 ? abs_sum / sum : 1e300;
+    const double kappa32 = sum > 0.0 ? abs_sum / sum : 1e300;
+    const double kappa64 = rsum > 0.0 ? maj / rsum : 1e300;
     const int cm = closed_form_mask(g, k);
     int mask = 0;
-    if (!(cm & 1) && kappa <= kBernKmax32 / 2) mask |= 1;
-    if (!(cm & 2) && kappa <= kBernKmax64 / 2) mask |= 2;
+    if (!(cm & 1) && prod_form < 0.9 * series && kappa32 <= kBernKmax32 / 2) mask |= 1;
+    if (!(cm & 2) && sum_form < 0.9 * series && kappa64 <= kBernKmax64 / 2) mask |= 2;
     return mask;
 }
 
@@ -225,7 +245,8 @@ s3_status plan_bernoulli(s3_graph_s *g) {
             // per lane: the x values, plus (FP64) the member ids staged during the gather
             lane = std::max(lane, d ? hb.s + (hb.s + 1) / 2 : hb.s);
             fb = std::max(fb, (int)warp_smem_elems(hb.s, t.W));
-            g->bern_cost[d] += (double)hb.m * ((double)hb.s * t.W * (t.W - 1) / 2.0 + 60.0 * hb.s);
+            g->bern_cost[d] += (double)hb.m * ((d ? 2.0 * hb.s * (t.W - 1) + (double)t.W * (t.W - 1)
+                                                  : (double)hb.s * t.W * (t.W - 1) / 2.0) + 60.0 * hb.s);
             tab.push_back(t);
         }
         if (bern_smem_bytes(lane, fb, d ? 8 : 4) > kEdgeSmemCap) {

@@ -17,7 +17,7 @@ struct BatchBucket {
     EdgeBucketArgs b;
     int32_t graph;
     int32_t W;
-    int32_t warp;  // 1: one warp per edge
+    int32_t warp;  // 0: one thread per edge (series), 1: one warp per edge, 2: size 1, 3: Bernoulli form
     int32_t pad;
 };
 
@@ -37,6 +37,9 @@ struct BatchEdgeArgs {
     int32_t per_warp;       // warp tiles: elements of T per warp
     unsigned long long *counter;
     unsigned long long *range_events;
+    int32_t bern_lane;      // Bernoulli tiles: values per lane of a warp's region
+    int32_t bern_fb;        // Bernoulli tiles: values of the warp's series-fallback region
+    BernArgs bern;          // Bernoulli constants (s3_bern.cuh)
 };
 
 // per-graph reduce tables (the partial and skip fields are unused here)
@@ -101,6 +104,7 @@ struct s3_batch_s {
     void *d_buf_mem[2] = {nullptr, nullptr};   // per dtype: all per-(graph, vector) buffers
     void *d_part_mem = nullptr;
     std::vector<int64_t> buf_off;              // element offset of each (graph, vector) buffer
+    int32_t bern_lane = 0, bern_fb = 0;        // Bernoulli tiles' per-warp shared memory (values)
     std::vector<int64_t> part_off;
     int64_t buf_elems = 0, part_elems = 0;
     size_t smem = 0;

@@ -70,6 +70,19 @@ s3_status build_tiles(s3_batch_s *bt, int elem_bytes) {
     bt->bucket_cost.clear();
     size_t smem = 0;
     const int bs = bt->bs;
+    // the buckets each graph evaluates in the Bernoulli form for this element type, and the
+    // per-warp shared memory those tiles need (one size for all of them)
+    const int bern_bit = elem_bytes == 4 ? 1 : 2;
+    bt->bern_lane = 0;
+    bt->bern_fb = 0;
+    for (s3_graph_s *g : bt->graphs)
+        for (size_t k = 0; k < g->buckets.size(); ++k)
+            if (k < g->bern_mask.size() && (g->bern_mask[k] & bern_bit) && g->buckets[k].m > 0) {
+                const int s = g->buckets[k].s;
+                bt->bern_lane = std::max(bt->bern_lane, elem_bytes == 4 ? s : s + (s + 1) / 2);
+                bt->bern_fb = std::max(bt->bern_fb, (int32_t)warp_smem_elems(s, g->N - s + 1));
+            }
+    const size_t bern_block = (size_t)(bs / 32) * ((size_t)32 * bt->bern_lane + bt->bern_fb) * elem_bytes;
     for (size_t gi = 0; gi < bt->graphs.size(); ++gi) {
         s3_graph_s *g = bt->graphs[gi];
         for (size_t k = 0; k < g->buckets.size(); ++k) {
@@ -92,14 +105,18 @@ s3_status build_tiles(s3_batch_s *bt, int elem_bytes) {
                                  (size_t)24 * hb.s;  // per thread
             bb.warp = (bb.W > bt->thread_max_w || need_thread * bs > 200 * 1024) ? 1 : 0;
             if (hb.s == 1) bb.warp = 2;
-            if (bb.warp == 1) {
+            if (k < g->bern_mask.size() && (g->bern_mask[k] & bern_bit) && bern_block <= 200 * 1024) bb.warp = 3;
+            if (bb.warp == 3) {
+                smem = std::max(smem, bern_block);
+            } else if (bb.warp == 1) {
                 int64_t pw = warp_smem_elems(std::max(hb.s, 1), bb.W);
                 smem = std::max(smem, (size_t)(bs / 32) * (size_t)pw * elem_bytes);
             } else {
                 smem = std::max(smem, need_thread * bs);
             }
             double W = bb.W;
-            double fma = hb.s >= 3 ? (2.0 * hb.s - 5.0) * W * (W + 1) / 2 + hb.s * W : 2 * W;
+            double fma = bb.warp == 3 ? (elem_bytes == 4 ? hb.s * W * (W - 1) / 2 : 2.0 * hb.s * W + W * (W - 1))
+                         : hb.s >= 3 ? (2.0 * hb.s - 5.0) * W * (W + 1) / 2 + hb.s * W : 2 * W;
             bt->bucket_cost.push_back(fma + 60.0 * hb.s);
             bt->h_buckets.push_back(bb);
         }
@@ -115,6 +132,7 @@ s3_status build_tiles(s3_batch_s *bt, int elem_bytes) {
         const BatchBucket &bb = bt->h_buckets[bi];
         size_t per_block;
         if (bb.warp == 2) per_block = 0;
+        else if (bb.warp == 3) per_block = bern_block;
         else if (bb.warp == 1) per_block = (size_t)(bs / 32) * (size_t)warp_smem_elems(bb.b.s, bb.W) * elem_bytes;
         else per_block = ((size_t)(2 * bb.b.s + (bb.b.s > 2 ? (bb.b.s - 2) * bb.W : 0)) * elem_bytes +
                           (size_t)24 * bb.b.s) * bs;

@@ -6,6 +6,7 @@
 #include <algorithm>
 
 #include "s3_batch.h"
+#include "s3_bern.cuh"
 #include "s3_series.cuh"
 
 namespace s3 {
@@ -94,6 +95,30 @@ __device__ __forceinline__ void batch_warp_tile(const BatchEdgeArgs &a, const Ba
     }
 }
 
+// Bernoulli-form tiles (s3_bern.cuh): one edge per thread, every vector of the graph in
+// turn; each warp's region holds a.bern_lane values per lane and a.bern_fb for the fallback.
+template <typename T, int W>
+__device__ __forceinline__ void batch_bern_tile(const BatchEdgeArgs &a, const BatchBucket &bb, const Tile &tl,
+                                                unsigned char *smem_raw) {
+    T *base = reinterpret_cast<T *>(smem_raw) +
+              (size_t)(threadIdx.x >> 5) * ((size_t)kLS * a.bern_lane + (size_t)a.bern_fb);
+    T *fb = base + (size_t)kLS * a.bern_lane;
+    EdgeOutArgs o{};
+    o.mode = kOutBuffer;
+    o.range_events = a.range_events;
+    const int64_t end = tl.e0 + tl.count;
+    for (int64_t e0 = tl.e0; e0 < end; e0 += blockDim.x) {
+        const int64_t e = e0 + threadIdx.x;
+        const bool valid = e < end;
+        if (__all_sync(0xffffffffu, !valid)) break;
+        for (int v = 0; v < a.nvec; ++v) {
+            o.out = a.bufs[(size_t)bb.graph * a.nvec + v];
+            const T *x = reinterpret_cast<const T *>(a.xs[(size_t)bb.graph * a.nvec + v]);
+            bern_edge<T, W, true>(bb.b, x, o, a.bern, e, valid, base, fb);
+        }
+    }
+}
+
 // Size-1 edges: c(e, v) = x_v^(N-1), one thread per edge and vector.
 template <typename T>
 __device__ __forceinline__ void batch_single_tile(const BatchEdgeArgs &a, const BatchBucket &bb, const Tile &tl) {
@@ -129,6 +154,14 @@ __global__ void __launch_bounds__(256) batch_edge_kernel(BatchEdgeArgs a) {
         const BatchBucket bb = a.buckets[tl.bucket];
         if (bb.warp == 2) {
             batch_single_tile<T>(a, bb, tl);
+        } else if (bb.warp == 3) {
+            switch (bb.W) {
+#define S3_BB_CASE(w) \
+    case w: batch_bern_tile<T, w>(a, bb, tl, smem_raw); break;
+                S3_W_CASES(S3_BB_CASE)
+#undef S3_BB_CASE
+                default: break;
+            }
         } else if (bb.warp) {
             batch_warp_tile<T>(a, bb, tl, smem_raw);
         } else {
@@ -326,6 +359,9 @@ s3_status record_batch_t(s3_batch_s *bt, cudaStream_t st) {
             ea.per_warp = per_warp;
             ea.counter = bt->d_counters + c;
             ea.range_events = bt->graphs.empty() ? nullptr : bt->graphs[0]->d_range;
+            ea.bern_lane = bt->bern_lane;
+            ea.bern_fb = bt->bern_fb;
+            if (!bt->graphs.empty()) ea.bern = bt->graphs[0]->bern_args;   // constants; rejections counted there
             int per_sm = 0;
             S3_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_edge_kernel<T>, bt->bs,
                                                                   bt->cls[c].smem));

@@ -9,22 +9,28 @@
 // numbers, B_1 = +1/2), the per-(edge, node) value of Algorithm 2 is
 //     [t^(N-1)] E(x_i t) prod_{j != i} Ebar(x_j t)
 //         = (prod_{j != i} x_j) * sum_{k=0}^{W-1} G[W-1-k] beta_k x_i^k.
-// G takes one truncated product per member (W(W-1)/2 multiply-adds each), and
-// every member then needs one short polynomial in x_i: about s W^2 / 2
-// operations per edge against the prefix/suffix scheme's (2s - 5) W^2 / 2, and
-// no stored prefix windows (per thread only the edge's x and scalar prefix
-// products live in shared memory).
+// Every member then needs one short polynomial in x_i, and only the edge's x stay
+// in shared memory (no stored prefix windows).  G is formed in one of two ways:
+//   * FP32: the product of the members' series, each step W independent Horner
+//     chains of W(W-1)/2 multiply-adds in all (about half of the prefix/suffix
+//     scheme's (2s - 5) W^2 / 2 per edge, with the same parallelism);
+//   * FP64: from the power sums p_k = sum_j x_j^k.  d/dt log g_x(t) =
+//     sum_{k>=1} beta_k x^k t^(k-1), so G = exp(sum_k beta_k p_k t^k / k), i.e.
+//     G_0 = 1, G_m = (1/m) sum_{k=1}^{m} beta_k p_k G_{m-k}: 2 (W-1) operations per
+//     member and W(W-1)/2 multiply-adds once per edge -- fewer operations for the
+//     FP64 pipe, less parallelism (the FP32 units measured faster with the product).
 //
-// The coefficients of G are sums of positive terms (x >= 0), but beta_k
-// alternates in sign for even k >= 4, so the final sum can cancel.  With
-// P = the sum of its positive terms and Q = the magnitude of its negative ones,
-// the value is P - Q and kappa = (P + Q) / (P - Q) bounds how much the relative
-// error of G and of the sum is amplified.  An edge is accepted when every
-// member has kappa <= kappa_max (BernArgs; 4 for FP32, 64 for FP64) and all its
-// x are >= 0; otherwise the warp recomputes it with the prefix/suffix series
-// (warp_edge_compute), so results are never less accurate than kappa_max times
-// the positive-term error.  For near-equal x, kappa stays below 1.2 for s >= 6
-// at rank 25 (below 2.2 when one member is twice the others).
+// beta_k alternates in sign for even k >= 4, so the final sum (and in FP64 the
+// recurrence) can cancel.  FP32: with P the positive terms of the sum and Q the
+// magnitude of the negative ones (G's coefficients are sums of positive terms, so
+// P + Q bounds the error mass), an edge is accepted when every member has
+// P + Q <= 4 (P - Q).  FP64: the recurrence runs a second time with |beta_k| (all
+// terms >= 0; its result A bounds the rounding error of G coefficient by
+// coefficient) and an edge is accepted when every member has
+// sum_k A[W-1-k] |beta_k| x_i^k <= 64 (P - Q).  Edges that fail, or hold an x <= 0,
+// are recomputed by the warp with the prefix/suffix series (warp_edge_compute).
+// For equal x at rank 25 the FP32 ratio is at most 1.15 for s >= 6 (2.1 with one
+// member twice the others), the FP64 ratio at most 2.2.
 #pragma once
 
 #include "s3_series.cuh"
@@ -52,6 +58,18 @@ __device__ __forceinline__ void bern_eval(const T (&H)[W], T xi, T &P, T &Q) {
         q = q * x4;
     }
     Q = q;
+}
+
+// sum_k Ha[k] x^k for the nonnegative coefficients Ha (Ha[k] = 0 for odd k >= 3): Horner in x^2
+// over the even k, plus the k = 1 term.
+template <typename T, int W>
+__device__ __forceinline__ T bern_majorant(const T (&Ha)[W], T xi) {
+    const T x2 = xi * xi;
+    T a = T(0);
+#pragma unroll
+    for (int k = 2 * ((W - 1) / 2); k >= 0; k -= 2) a = Arith<T>::fma_(a, x2, Ha[k]);
+    if constexpr (W > 1) a = Arith<T>::fma_(Ha[1], xi, a);
+    return a;
 }
 
 template <typename T> __device__ __forceinline__ T bern_beta(const BernArgs &c, int k);
@@ -101,46 +119,104 @@ __device__ __forceinline__ void bern_edge(const EdgeBucketArgs &b, const T *__re
         }
         p = scale_exponent<T>(S, b.target);
         const T g = Arith<T>::pow2(p);
-        // G = g_{x_1} (its coefficients x^k / (k+1)!), then times g_{x_i}, i = 2..s;
-        // P = the product of all (scaled) x
-        T G[W];
-        T prod;
-        {
-            const T x0 = xs[0] * g;
-            xs[0] = x0;
-            prod = x0;
-            G[0] = T(1);
-#pragma unroll
-            for (int k = 1; k < W; ++k) G[k] = G[k - 1] * (x0 * Num<T>::recip(k + 1));
-        }
-        for (int i = 1; i < s; ++i) {
-            const T xi = xs[i * kLS] * g;
-            xs[i * kLS] = xi;
-            prod *= xi;
-            T r[W];
-#pragma unroll
-            for (int k = 1; k < W; ++k) r[k] = xi * Num<T>::recip(k + 1);
-            // G[m] <- G[m] + r_1 (G[m-1] + r_2 (G[m-2] + ... + r_m G[0])), top down in place
-#pragma unroll
-            for (int m = W - 1; m >= 1; --m) {
-                T t = G[0];
-#pragma unroll
-                for (int j = 1; j <= m; ++j) t = Arith<T>::fma_(r[m - j + 1], t, G[j]);
-                G[m] = t;
+        if constexpr (sizeof(T) == 4) {
+            // G = g_{x_1} (its coefficients x^k / (k+1)!), then times g_{x_i}, i = 2..s, each product
+            // in Horner form (W independent chains); P = the product of all (scaled) x
+            T G[W];
+            T prod;
+            {
+                const T x0 = xs[0] * g;
+                xs[0] = x0;
+                prod = x0;
+                G[0] = T(1);
+    #pragma unroll
+                for (int k = 1; k < W; ++k) G[k] = G[k - 1] * (x0 * Num<T>::recip(k + 1));
             }
-        }
-        T H[W];
-#pragma unroll
-        for (int k = 0; k < W; ++k) H[k] = G[W - 1 - k] * bern_beta<T>(c, k);
-        const T kmax = bern_kmax<T>(c);
-        // every member: the Bernoulli sum (gate), times prod_{j != i} x_j = P / x_i (all x > 0)
-        for (int i = 0; i < s; ++i) {
-            const T xi = xs[i * kLS];
-            T Pp, Q;
-            bern_eval<T, W>(H, xi, Pp, Q);
-            const T v = Pp - Q;
-            ok &= (Pp + Q) <= kmax * v;
-            xs[i * kLS] = v * (prod / xi);
+            for (int i = 1; i < s; ++i) {
+                const T xi = xs[i * kLS] * g;
+                xs[i * kLS] = xi;
+                prod *= xi;
+                T r[W];
+    #pragma unroll
+                for (int k = 1; k < W; ++k) r[k] = xi * Num<T>::recip(k + 1);
+                // G[m] <- G[m] + r_1 (G[m-1] + r_2 (G[m-2] + ... + r_m G[0])), top down in place
+    #pragma unroll
+                for (int m = W - 1; m >= 1; --m) {
+                    T t = G[0];
+    #pragma unroll
+                    for (int j = 1; j <= m; ++j) t = Arith<T>::fma_(r[m - j + 1], t, G[j]);
+                    G[m] = t;
+                }
+            }
+            T H[W];
+    #pragma unroll
+            for (int k = 0; k < W; ++k) H[k] = G[W - 1 - k] * bern_beta<T>(c, k);
+            const T kmax = bern_kmax<T>(c);
+            // every member: the Bernoulli sum (G's coefficients are exact sums of positive terms
+            // up to rounding, so P + Q bounds the error mass), times prod_{j != i} x_j = P / x_i
+            for (int i = 0; i < s; ++i) {
+                const T xi = xs[i * kLS];
+                T Pp, Q;
+                bern_eval<T, W>(H, xi, Pp, Q);
+                const T v = Pp - Q;
+                ok &= (Pp + Q) <= kmax * v;
+                xs[i * kLS] = v * (prod / xi);
+            }
+        } else {
+            // power sums p_k = sum_j x_j^k (k = 1..W-1, in q[k]) and P = prod_j x_j; each member's
+            // powers by a binary tree (x^k = x^(k/2) x^(k - k/2)), so their dependency depth is log2 W
+            T q[W];
+    #pragma unroll
+            for (int k = 0; k < W; ++k) q[k] = T(0);
+            T prod = T(1);
+            for (int i = 0; i < s; ++i) {
+                const T xi = xs[i * kLS] * g;
+                xs[i * kLS] = xi;
+                prod *= xi;
+                T pw[W];
+                pw[0] = T(1);
+                if constexpr (W > 1) pw[1] = xi;
+    #pragma unroll
+                for (int k = 2; k < W; ++k) pw[k] = pw[k / 2] * pw[k - k / 2];
+    #pragma unroll
+                for (int k = 1; k < W; ++k) q[k] += pw[k];
+            }
+            // G = exp(sum_k l_k p_k t^k) with k l_k = beta_k: G_0 = 1,
+            // G_m = (1/m) sum_{k=1}^{m} beta_k p_k G_{m-k}; A the same recurrence with |beta_k|
+            // (all terms >= 0), which bounds the rounding error of G
+    #pragma unroll
+            for (int k = 1; k < W; ++k) q[k] *= bern_beta<T>(c, k);
+            T G[W], A[W];
+            G[0] = T(1);
+            A[0] = T(1);
+    #pragma unroll
+            for (int m = 1; m < W; ++m) {
+                // from k = m down, so that G[m-1] (the value just formed) enters last
+                T acc = T(0), acca = T(0);
+    #pragma unroll
+                for (int k = m; k >= 1; --k) {
+                    acc = Arith<T>::fma_(q[k], G[m - k], acc);
+                    acca = Arith<T>::fma_(Arith<T>::absv(q[k]), A[m - k], acca);
+                }
+                G[m] = acc * Num<T>::recip(m);
+                A[m] = acca * Num<T>::recip(m);
+            }
+            T H[W], Ha[W];
+    #pragma unroll
+            for (int k = 0; k < W; ++k) {
+                H[k] = G[W - 1 - k] * bern_beta<T>(c, k);
+                Ha[k] = A[W - 1 - k] * Arith<T>::absv(bern_beta<T>(c, k));
+            }
+            const T kmax = bern_kmax<T>(c);
+            // every member: the Bernoulli sum, its majorant (gate), times prod_{j != i} x_j = P / x_i
+            for (int i = 0; i < s; ++i) {
+                const T xi = xs[i * kLS];
+                T Pp, Q;
+                bern_eval<T, W>(H, xi, Pp, Q);
+                const T v = Pp - Q;
+                ok &= bern_majorant<T, W>(Ha, xi) <= kmax * v;
+                xs[i * kLS] = v * (prod / xi);
+            }
         }
         ok &= pos;
     }
@@ -165,7 +241,8 @@ __device__ __forceinline__ void bern_edge(const EdgeBucketArgs &b, const T *__re
                 if (sc.fast) {
                     emit_fast<T, BUF>(o, t, val, sc.mult, nbad);
                 } else {
-                    // scaled x of the member (its exponent sets the per-node bias of NQZ)
+                    // scaled x of the member (its exponent sets the per-node bias of NQZ): reloaded
+                    // here, off the common path
                     const T xhat = __ldg(x + __ldg(b.ids + (int64_t)i * b.ld + e)) * Arith<T>::pow2(p);
                     emit_value<T, BUF>(b, o, t, t, val, p, xhat);
                 }
@@ -183,8 +260,8 @@ __device__ __forceinline__ void bern_edge(const EdgeBucketArgs &b, const T *__re
 }
 
 // All Bernoulli buckets of a call in one launch: block ranges map to buckets
-// (TailEntry::block0 ascending), one edge per thread.  Per warp: lane_elems
-// values per lane, then fb_elems values for the series fallback.
+// (TailEntry::block0 ascending), one edge per thread.  Per warp: lane_elems values per
+// lane, then fb_elems values for the series fallback.
 template <typename T, bool BUF>
 __global__ void __launch_bounds__(kBernThreads, sizeof(T) == 4 ? 7 : 3) edge_bern_kernel(const TailEntry *__restrict__ tab, int ntab,
                                                                  int lane_elems, int fb_elems,

@@ -86,7 +86,10 @@ struct s3_graph_s {
     cudaEvent_t ev_done = nullptr;
     cudaStream_t qstream = nullptr;
     unsigned long long *h_range = nullptr;
-    uint32_t *d_feat_scratch = nullptr;  // warm-start feature counters (48 bytes per node)
+    uint32_t *d_feat_scratch = nullptr;  // warm-start feature partials (64 bytes per hub piece)
+    s3::TailEntry *d_feat_tab = nullptr; // buckets of the fused feature launch (size bin in W)
+    int32_t n_feat_tab = 0;
+    int64_t feat_blocks = 0;
     float *d_ws = nullptr;               // warm-start features, predictions, partials
     // concurrent buckets: forked streams and events, bucket order (heaviest first) and cost
     int n_streams = 1;

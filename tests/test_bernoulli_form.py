@@ -4,16 +4,23 @@ The Bernoulli kernels evaluate, for an edge e of size s at rank N (W = N-s+1),
     c(e, v_i) / K(s,N) = (prod_{j != i} x_j) * sum_{k<W} G[W-1-k] beta_k x_i^k,
 with G = prod_j g_{x_j} truncated to W coefficients, g_x(t) = (e^(x t) - 1)/(x t),
 and beta_k = B_k^+ / k! the coefficients of z / (1 - e^(-z)).  That rests on
-E(x t) / Ebar(x t) = 1 / (1 - e^(-x t)) (Sec. II-A's E and Ebar).  These tests
+E(x t) / Ebar(x t) = 1 / (1 - e^(-x t)) (Sec. II-A's E and Ebar).  G itself is
+formed from the power sums p_k = sum_j x_j^k: log g_x(t) has the coefficients
+beta_k x^k / k (its derivative is sum_k beta_k x^k t^(k-1)), so G = exp(sum_k
+beta_k p_k t^k / k), i.e. G_0 = 1, G_m = (1/m) sum_{k=1}^m beta_k p_k G_{m-k}.
+These tests
   * check beta_k against the Bernoulli numbers B_k (exact rationals, from their
     defining recurrence),
-  * check the identity in exact rationals against the oracle's generating-function
-    value of Algorithm 2, for edges of every size at several ranks, zeros included,
-  * replay the kernels' FP32 operation order in numpy float32 (the same Horner
-    forms, the x^4-Horner split of the sum into its positive part P and negative
-    part Q, prefix and suffix products) and check that every member the gate
-    (P + Q <= 4 (P - Q)) accepts is within the FP32 tolerance of the exact value,
-    and that the gate rejects the badly conditioned edges.
+  * check both identities in exact rationals -- the recurrence against the
+    product, and the per-member sum against the oracle's generating-function
+    value of Algorithm 2 -- for edges of every size at several ranks, zeros included,
+  * replay the FP32 kernel's operation order in numpy float32 (G as a product of
+    the members' series in Horner form, the x^4-Horner split of the sum into its
+    positive part P and negative part Q, P / x_i) and check that every member the
+    gate (P + Q <= 4 (P - Q)) accepts is within the FP32 tolerance of the exact
+    value, and that the gate rejects badly conditioned edges.  (The FP64 kernel
+    forms G by the power-sum recurrence, checked exactly here and against the
+    oracle at 1e-12 on the GPU.)
 The GPU tests check the kernels themselves against the oracle.
 """
 from fractions import Fraction
@@ -49,6 +56,24 @@ def test_beta_is_the_series_of_z_over_one_minus_exp():
         assert sum(beta[k] * f[m - k] for k in range(m + 1)) == (1 if m == 0 else 0)
     assert beta[:5] == [1, Fraction(1, 2), Fraction(1, 12), 0, Fraction(-1, 720)]
     assert all(beta[k] == 0 for k in range(3, 32, 2))
+
+
+@pytest.mark.parametrize("N", [8, 17, 25])
+def test_power_sum_recurrence_is_the_product(N):
+    rng = np.random.default_rng(N + 100)
+    for s in range(2, N + 1):
+        W = N - s + 1
+        beta = beta_exact(max(W - 1, 1))
+        xs = [Fraction(int(v), 16) for v in rng.integers(1, 40, size=s)]
+        G = [Fraction(1)] + [Fraction(0)] * (W - 1)
+        for xj in xs:
+            g = [xj ** k / factorial(k + 1) for k in range(W)]
+            G = [sum(G[m - k] * g[k] for k in range(m + 1)) for m in range(W)]
+        p = [sum(xj ** k for xj in xs) for k in range(W)]
+        R = [Fraction(1)] + [Fraction(0)] * (W - 1)
+        for m in range(1, W):
+            R[m] = sum(beta[k] * p[k] * R[m - k] for k in range(1, m + 1)) / m
+        assert R == G, (N, s)
 
 
 def bern_exact(xs, i, N):

@@ -39,10 +39,11 @@ def test_batched_equals_single_calls(dtype):
             ref = torch.empty_like(x)
             s3.s3_sttsvc(gs[j // nvec], x, ref)
             torch.cuda.synchronize()
-            # same kernels and summation order, except that a bucket may be computed by a
-            # warp per edge in one path and a thread per edge in the other (shared-memory caps)
+            # the single calls may evaluate large buckets in closed form, the batched kernels
+            # never do: both within the parity tolerance of the exact values, so within twice
+            # of each other
             e = rel_err(y.double().cpu().numpy(), ref.double().cpu().numpy(), floor=1e-30)
-            assert e <= (2e-6 if dtype == "f32" else 1e-14), f"graph {j // nvec} vector {j % nvec}: {e:.2e}"
+            assert e <= (2e-5 if dtype == "f32" else 2e-12), f"graph {j // nvec} vector {j % nvec}: {e:.2e}"
     # one graph all the way to the oracle
     want = oracle.ttsv1(hgs[2], xs[2 * nvec + 1].double().cpu().numpy())
     tol = 1e-5 if dtype == "f32" else 1e-12
@@ -77,6 +78,42 @@ def test_batched_without_graph_and_autotune():
     s3.s3_sttsvc_batched(b, xs, ys2)
     torch.cuda.synchronize()
     assert all(torch.equal(y, r) for y, r in zip(ys2, refs))
+
+
+@pytest.mark.parametrize("dtype", ["f32", "f64"])
+def test_batched_bernoulli_tiles(dtype):
+    # Bernoulli-form buckets run as Bernoulli tiles in the batched kernel, with the same
+    # per-edge arithmetic (and the same series fallback) as the single calls' launch.  FP32:
+    # the other buckets run the same series kernels too, so the results are equal bit for
+    # bit.  FP64: single calls run sizes 2 and 3 in kernels of their own; every vector
+    # against the oracle at the FP64 bound instead
+    import torch
+
+    import paper_2311_08595_gb300 as s3
+    dt = torch.float32 if dtype == "f32" else torch.float64
+    hgs = _graphs()[:4]
+    gs = [s3.s3_build_format(h.n, h.edge_ptr, h.members, closed_form_max_s=0) for h in hgs]
+    used = [s3.s3_bernoulli_query(g)[dtype] for g in gs]
+    assert sum(len(u) for u in used) > 0, used
+    nvec = 2
+    xs = [torch.tensor(s3synth.x_uniform(h.n, 0.5, 1.5, 11 * gi + v), dtype=dt, device="cuda")
+          for gi, h in enumerate(hgs) for v in range(nvec)]
+    refs = []
+    for j, x in enumerate(xs):
+        r = torch.empty_like(x)
+        s3.s3_sttsvc(gs[j // nvec], x, r)
+        refs.append(r)
+    b = s3.s3_batch_create(gs, nvec)
+    ys = [torch.full_like(x, float("nan")) for x in xs]
+    for _ in range(2):
+        s3.s3_sttsvc_batched(b, xs, ys)
+        torch.cuda.synchronize()
+        if dtype == "f32":
+            assert all(torch.equal(y, r) for y, r in zip(ys, refs))
+        else:
+            for j, y in enumerate(ys):
+                want = oracle.ttsv1(hgs[j // nvec], xs[j].cpu().numpy())
+                assert rel_err(y.cpu().numpy(), want) <= 1e-12, j
 
 
 def test_batch_rejects_atomic_graphs():

@@ -94,8 +94,8 @@ def test_rejected_edges_go_back_to_the_series(dt, tol):
 
 
 def test_bernoulli_large_rank_and_small_tiles():
-    # rank 40: the Bernoulli form covers sizes 9..40 (windows <= 32); a few edges of each
-    # size, so every bucket ends in a partial warp
+    # rank 40: the Bernoulli form covers sizes 9..40 (windows <= 32); a few edges of each size,
+    # so every bucket ends in a partial warp
     rng = np.random.default_rng(34)
     edges = [tuple(rng.choice(3000, size=s, replace=False)) for s in range(6, 41) for _ in range(int(rng.integers(1, 40)))]
     hg = s3synth.from_edges(3000, edges)
