@@ -49,7 +49,7 @@ def measured_peaks():
     return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
 
 
-def algorithmic_counts(edges_per_size, N, closed_sizes=(), bern_sizes=()):
+def algorithmic_counts(edges_per_size, N, closed_sizes=(), bern_sizes=(), bern_form="product"):
     """FLOPs of one FP32 S^3TTVc call by the edge-layout algorithm.
 
     Per edge of size s >= 2 with window W = N - s + 1 (series):
@@ -57,7 +57,8 @@ def algorithmic_counts(edges_per_size, N, closed_sizes=(), bern_sizes=()):
                          (s >= 3), plus W FMAs for the last suffix coefficient;
       dots: (W-1) for [t^(N-1)] F_e and W for each of the s-2 interior nodes;
       power tables: 2(s-1) tables of W coefficients, 2 multiplies per coefficient.
-    Sizes in bern_sizes count as bernoulli_flops gives them.
+    Sizes in bern_sizes count as bernoulli_flops gives them (bern_form: "product" for FP32,
+    "powersum" for FP64).
     Per edge of a size in closed_sizes (inclusion-exclusion): for each of the 2^s - 1
     subsets one add (its sum), floor(log2 n) + popcount(n) - 1 multiplies (sum^n,
     n = N-1) and one add (the sum of |terms|), then s 2^(s-1) signed adds.  The
@@ -77,7 +78,7 @@ def algorithmic_counts(edges_per_size, N, closed_sizes=(), bern_sizes=()):
             mul += cnt * ((2 ** s - 1) * (2 + n.bit_length() - 1 + bin(n).count("1") - 1) + s * 2 ** (s - 1))
             continue
         if s in bern_sizes:
-            mul += bernoulli_flops(edges_per_size, N, [s])
+            mul += bernoulli_flops(edges_per_size, N, [s], bern_form)
             continue
         W = N - s + 1
         f = (W - 1) + max(s - 2, 0) * W
@@ -88,22 +89,32 @@ def algorithmic_counts(edges_per_size, N, closed_sizes=(), bern_sizes=()):
     return 2 * fma + mul, fma
 
 
-def bernoulli_flops(edges_per_size, N, sizes):
+def bernoulli_flops(edges_per_size, N, sizes, form="product"):
     """FLOPs of the Bernoulli-form launch (csrc/s3_bern.cuh) for the edge sizes it takes.
 
-    Per edge of size s, window W = N - s + 1: the first member's series g (2(W-1)
-    multiplies), then per further member the ratios x/(k+1) (W-1 multiplies), the
-    truncated product (W(W-1)/2 multiply-adds) and the running product (1 multiply);
-    the coefficients H_k = G[W-1-k] beta_k (W multiplies); per member the sum in
-    x^4-Horner form (2 + 2 ceil((W-2)/4) + 2 ceil((W-4)/4) + 4 flops with x^2, x^4 and
-    the two leading terms), the gate (3) and P / x_i times the sum (2).  One
-    multiply-add = 2 flops."""
+    Per edge of size s, window W = N - s + 1, the product form (FP32): the first member's
+    series g (2(W-1) multiplies), then per further member the ratios x/(k+1) (W-1
+    multiplies), the truncated product (W(W-1)/2 multiply-adds) and the running product
+    (1 multiply); the coefficients H_k = G[W-1-k] beta_k (W multiplies); per member the
+    sum in x^4-Horner form (2 + 2 ceil((W-2)/4) + 2 ceil((W-4)/4) + 4 flops with x^2, x^4
+    and the two leading terms), the gate (3) and P / x_i times the sum (2).
+    The power-sum form (FP64): per member the scaling and running product (2), the powers
+    x^2..x^(W-1) (W-2 multiplies) and their sums (W-1 adds); beta_k p_k (W-1 multiplies);
+    the recurrences for G and its majorant A (for m = 1..W-1: 2m multiply-adds and 2
+    multiplies); H_k and A[W-1-k]|beta_k| (2W multiplies); per member the sum as above, the
+    majorant in x^2-Horner form (1 + 2 ceil(W/2) + 2 flops), the gate (2) and the value (2).
+    One multiply-add = 2 flops."""
     total = 0
     for s in sizes:
         cnt = edges_per_size[s]
         W = N - s + 1
-        per = 2 * (W - 1) + (s - 1) * ((W - 1) + W * (W - 1) + 1) + W
-        per += s * (4 + 2 * -(-max(W - 2, 0) // 4) + 2 * -(-max(W - 4, 0) // 4) + 2 + 3 + 2)
+        horner = 4 + 2 * -(-max(W - 2, 0) // 4) + 2 * -(-max(W - 4, 0) // 4) + 2
+        if form == "product":
+            per = 2 * (W - 1) + (s - 1) * ((W - 1) + W * (W - 1) + 1) + W
+            per += s * (horner + 3 + 2)
+        else:
+            per = s * (2 + (W - 2) + (W - 1)) + (W - 1) + 2 * W * (W - 1) + 2 * (W - 1) + 2 * W
+            per += s * (horner + (1 + 2 * -(-W // 2) + 2) + 2 + 2)
         total += cnt * per
     return total
 
@@ -390,13 +401,14 @@ def run_gpu(args):
     ms64 = _time_calls(g, x64, y64, 20)
     prof64 = [s3.s3_sttsvc_profile(g, x64, y64) for _ in range(3)]
     edge64 = float(np.mean([p["edge_ms"] for p in prof64]))
-    flops64, _ = algorithmic_counts(info["edges_per_size"], N, closed["f64"])
+    flops64, _ = algorithmic_counts(info["edges_per_size"], N, closed["f64"], bern["f64"], "powersum")
     out["fp64"] = {"value": nnz / (ms64 * 1e-3), "unit": UNIT, "ms_per_call": ms64, "calls_timed": 20,
                    "fp32_speedup": ms64 / ms,
                    "roofline": {"bound": "alu", "achieved": flops64 / (edge64 * 1e-3) / 1e12, "peak": p64["tflops"],
                                 "unit": "TFLOP/s", "frac": flops64 / (edge64 * 1e-3) / 1e12 / p64["tflops"],
-                                "edge_ms": edge64, "closed_form_sizes": closed["f64"],
+                                "edge_ms": edge64, "closed_form_sizes": closed["f64"], "bernoulli_sizes": bern["f64"],
                                 "peak_note": "of measured: FP64 FMA-chain probe (s3_fma_peak)"},
+                   "bernoulli_kernel": _bern64_roofline(prof64, info["edges_per_size"], N, bern["f64"], p64["tflops"]),
                    "hbm_bytes_per_call": hbm_bytes(nnz, n, esz=8)}
     # FP64 in and out with the series in double-float (pairs of FP32)
     ydf = torch.empty_like(y64)
@@ -522,6 +534,17 @@ def warm_start(lcc, dev, graphs=48, n=50000, epochs=20):
         out[name] = ws.evaluate(lcc, model, tol=1e-8, precision=prec)
     out["start_cost"] = ws.start_cost(lcc, model)
     return out
+
+
+def _bern64_roofline(prof, edges_per_size, N, sizes, peak):
+    """The FP64 Bernoulli launch (power-sum form) against the FP64 FMA peak."""
+    ms = float(np.mean([p["bern_ms"] for p in prof]))
+    fl = bernoulli_flops(edges_per_size, N, sizes, "powersum")
+    if ms <= 0 or not sizes:
+        return None
+    return {"kernel": "edge_bern_kernel<double>", "launch_ms": ms, "algorithmic_flops_per_launch": fl,
+            "achieved": fl / (ms * 1e-3) / 1e12, "peak": peak, "unit": "TFLOP/s",
+            "frac": fl / (ms * 1e-3) / 1e12 / peak}
 
 
 def _time_calls(g, x, y, reps, df=False):

@@ -53,7 +53,8 @@ typedef enum {
     S3_ENOMEM = 2,    /* device or host allocation failed */
     S3_ECUDA = 3,     /* a CUDA call failed (message in s3_last_error) */
     S3_ENOCONV = 4,   /* NQZ did not reach the tolerance within max_iter */
-    /* 5 is unused: no kernel of the library waits on a flag, a peer or a barrier */
+    S3_ETIMEOUT = 5,  /* a bounded device wait ran out (the MMA-completion wait of
+                         s3_mlp_forward; reported by the next s3_warmstart or s3_mlp_get_params) */
     S3_ERANGE = 6,    /* results left the range of the arithmetic type (synchronous and
                          range-checked calls, s3_options.range_check) */
     S3_ENOTSUP = 7    /* configuration not supported by this build */
@@ -459,7 +460,10 @@ s3_status s3_mlp_create(const float *params, uint64_t seed, s3_mlp_t *out);
 s3_status s3_mlp_get_params(s3_mlp_t m, float *params, int32_t bf16);
 
 /* out[v] = W3 relu(W2 relu(W1 feat_v + b1) + b2) + b3 with the BF16 weights and
- * FP32 accumulation.  feat: device n x 12; out: device n floats. */
+ * FP32 accumulation; the 64 x 64 layer on the tensor cores, its input split into two
+ * BF16 terms (relative error about 2^-17 against FP32 input).  feat: device n x 12;
+ * out: device n floats.  Asynchronous; a tensor-core wait that runs out (bounded, well
+ * under a second) is reported as S3_ETIMEOUT by the next synchronising call on the model. */
 s3_status s3_mlp_forward(s3_mlp_t m, const float *feat, int64_t n, float *out, void *stream);
 
 /*

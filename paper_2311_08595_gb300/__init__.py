@@ -20,7 +20,7 @@ import ctypes
 import numpy as np
 
 from . import _lib
-from ._lib import (S3_DF64, S3_EINVAL, S3_ENOCONV, S3_ENOTSUP, S3_ERANGE, S3_F32, S3_F64,  # noqa: F401
+from ._lib import (S3_DF64, S3_EINVAL, S3_ENOCONV, S3_ENOTSUP, S3_ERANGE, S3_ETIMEOUT, S3_F32, S3_F64,  # noqa: F401
                    S3_LAYOUT_CCSS, S3_LAYOUT_EDGE, S3_REDUCE_ATOMIC, S3_REDUCE_SEGMENTED, S3Error, check, load,
                    ptr)
 

@@ -17,8 +17,7 @@ LIB_PATH = os.path.join(HERE, "libs3ttvc.so")
 
 S3_MAX_RANK = 128
 S3_MLP_FEATURES, S3_MLP_HIDDEN, S3_MLP_PARAMS = 12, 64, 5057
-S3_OK, S3_EINVAL, S3_ENOMEM, S3_ECUDA, S3_ENOCONV = range(5)
-S3_ERANGE, S3_ENOTSUP = 6, 7
+S3_OK, S3_EINVAL, S3_ENOMEM, S3_ECUDA, S3_ENOCONV, S3_ETIMEOUT, S3_ERANGE, S3_ENOTSUP = range(8)
 S3_F32, S3_F64, S3_DF64 = 0, 1, 2
 S3_REDUCE_SEGMENTED, S3_REDUCE_ATOMIC = 0, 1
 S3_LAYOUT_EDGE, S3_LAYOUT_CCSS = 0, 1

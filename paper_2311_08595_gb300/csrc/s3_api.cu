@@ -901,6 +901,7 @@ const char *s3_status_string(s3_status st) {
         case S3_ENOMEM: return "S3_ENOMEM";
         case S3_ECUDA: return "S3_ECUDA";
         case S3_ENOCONV: return "S3_ENOCONV";
+        case S3_ETIMEOUT: return "S3_ETIMEOUT";
         case S3_ERANGE: return "S3_ERANGE";
         case S3_ENOTSUP: return "S3_ENOTSUP";
     }

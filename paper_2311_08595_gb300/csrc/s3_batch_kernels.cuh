@@ -114,7 +114,7 @@ __device__ __forceinline__ void batch_bern_tile(const BatchEdgeArgs &a, const Ba
         for (int v = 0; v < a.nvec; ++v) {
             o.out = a.bufs[(size_t)bb.graph * a.nvec + v];
             const T *x = reinterpret_cast<const T *>(a.xs[(size_t)bb.graph * a.nvec + v]);
-            bern_edge<T, W, true>(bb.b, x, o, a.bern, e, valid, base, fb);
+            bern_edge<T, W, true, false>(bb.b, x, o, a.bern, e, valid, base, fb);
         }
     }
 }

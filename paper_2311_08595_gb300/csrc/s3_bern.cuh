@@ -93,7 +93,7 @@ __device__ __noinline__ void bern_fallback(const EdgeBucketArgs &b, const T *__r
 // overwrites).  Shared memory is kept to that -- the x gathers also use the L1 cache,
 // which the rest of the shared-memory carve-out would take away.  fb: the warp's region
 // for the series fallback.
-template <typename T, int W, bool BUF>
+template <typename T, int W, bool BUF, bool BIAS>
 __device__ __forceinline__ void bern_edge(const EdgeBucketArgs &b, const T *__restrict__ x, const EdgeOutArgs &o,
                                           const BernArgs &c, int64_t e, bool valid, T *lane_base, T *fb) {
     const int lane = threadIdx.x & 31;
@@ -160,7 +160,13 @@ __device__ __forceinline__ void bern_edge(const EdgeBucketArgs &b, const T *__re
                 bern_eval<T, W>(H, xi, Pp, Q);
                 const T v = Pp - Q;
                 ok &= (Pp + Q) <= kmax * v;
-                xs[i * kLS] = v * (prod / xi);
+                if constexpr (BIAS) {
+                    // the biased output of the centrality iteration: the scale of each result
+                    // depends on its member's exponent, which is at hand here
+                    xs[i * kLS] = scale_result<T>(v * (prod / xi), b, p, Arith<T>::expo(xi) - p, nullptr);
+                } else {
+                    xs[i * kLS] = v * (prod / xi);
+                }
             }
         } else {
             // power sums p_k = sum_j x_j^k (k = 1..W-1, in q[k]) and P = prod_j x_j; each member's
@@ -215,7 +221,13 @@ __device__ __forceinline__ void bern_edge(const EdgeBucketArgs &b, const T *__re
                 bern_eval<T, W>(H, xi, Pp, Q);
                 const T v = Pp - Q;
                 ok &= bern_majorant<T, W>(Ha, xi) <= kmax * v;
-                xs[i * kLS] = v * (prod / xi);
+                if constexpr (BIAS) {
+                    // the biased output of the centrality iteration: the scale of each result
+                    // depends on its member's exponent, which is at hand here
+                    xs[i * kLS] = scale_result<T>(v * (prod / xi), b, p, Arith<T>::expo(xi) - p, nullptr);
+                } else {
+                    xs[i * kLS] = v * (prod / xi);
+                }
             }
         }
         ok &= pos;
@@ -238,7 +250,12 @@ __device__ __forceinline__ void bern_edge(const EdgeBucketArgs &b, const T *__re
                 if (i >= s) break;
                 const T val = xs[i * kLS];
                 const int t = tv[j];
-                if (sc.fast) {
+                if constexpr (BIAS) {
+                    // scaled already (every x > 0, so every value is positive)
+                    nbad += not_normal_pos(val);
+                    if constexpr (BUF) reinterpret_cast<T *>(o.out)[t] = val;
+                    else scatter_atomic<T>(o, t, val);
+                } else if (sc.fast) {
                     emit_fast<T, BUF>(o, t, val, sc.mult, nbad);
                 } else {
                     // scaled x of the member (its exponent sets the per-node bias of NQZ): reloaded
@@ -262,7 +279,7 @@ __device__ __forceinline__ void bern_edge(const EdgeBucketArgs &b, const T *__re
 // All Bernoulli buckets of a call in one launch: block ranges map to buckets
 // (TailEntry::block0 ascending), one edge per thread.  Per warp: lane_elems values per
 // lane, then fb_elems values for the series fallback.
-template <typename T, bool BUF>
+template <typename T, bool BUF, bool BIAS>
 __global__ void __launch_bounds__(kBernThreads, sizeof(T) == 4 ? 7 : 3) edge_bern_kernel(const TailEntry *__restrict__ tab, int ntab,
                                                                  int lane_elems, int fb_elems,
                                                                  const T *__restrict__ x, EdgeOutArgs o, BernArgs c) {
@@ -279,33 +296,36 @@ __global__ void __launch_bounds__(kBernThreads, sizeof(T) == 4 ? 7 : 3) edge_ber
     T *fb = base + (size_t)kLS * lane_elems;
     switch (tab[k].W) {
 #define S3_BERN_CASE(w) \
-    case w: bern_edge<T, w, BUF>(b, x, o, c, e, valid, base, fb); break;
+    case w: bern_edge<T, w, BUF, BIAS>(b, x, o, c, e, valid, base, fb); break;
         S3_W_CASES(S3_BERN_CASE)
 #undef S3_BERN_CASE
         default: break;
     }
 }
 
-template <typename T>
+// Launch for the output modes of one BIAS value (the biased centrality mode, or not): each
+// value is instantiated in a translation unit of its own, to keep their compile times apart.
+template <typename T, bool BIAS>
 cudaError_t launch_edge_bern_t(const TailEntry *tab, int ntab, int64_t nblocks, int lane_elems, int fb_elems,
                                const T *x, const EdgeOutArgs &o, const BernArgs &c, cudaStream_t st) {
     if (ntab <= 0 || nblocks <= 0) return cudaSuccess;
     const size_t smem = bern_smem_bytes(lane_elems, fb_elems, sizeof(T));
-    if (smem > kEdgeSmemCap || nblocks > INT32_MAX) return cudaErrorInvalidConfiguration;
+    if (smem > kEdgeSmemCap || nblocks > INT32_MAX || (o.bias != 0) != BIAS) return cudaErrorInvalidConfiguration;
+    const dim3 grid((unsigned)nblocks), block(kBernThreads);
     if (o.mode == kOutBuffer)
-        edge_bern_kernel<T, true><<<(unsigned)nblocks, kBernThreads, smem, st>>>(tab, ntab, lane_elems, fb_elems, x, o, c);
+        edge_bern_kernel<T, true, BIAS><<<grid, block, smem, st>>>(tab, ntab, lane_elems, fb_elems, x, o, c);
     else
-        edge_bern_kernel<T, false><<<(unsigned)nblocks, kBernThreads, smem, st>>>(tab, ntab, lane_elems, fb_elems, x, o, c);
+        edge_bern_kernel<T, false, BIAS><<<grid, block, smem, st>>>(tab, ntab, lane_elems, fb_elems, x, o, c);
     return cudaGetLastError();
 }
 
-template <typename T>
+template <typename T, bool BIAS>
 cudaError_t prepare_edge_bern_t() {
-    cudaError_t e = cudaFuncSetAttribute(edge_bern_kernel<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)kEdgeSmemCap);
-    if (e != cudaSuccess) return e;
-    return cudaFuncSetAttribute(edge_bern_kernel<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)kEdgeSmemCap);
+    const int cap = (int)kEdgeSmemCap;
+    cudaError_t e = cudaFuncSetAttribute(edge_bern_kernel<T, true, BIAS>, cudaFuncAttributeMaxDynamicSharedMemorySize, cap);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(edge_bern_kernel<T, false, BIAS>, cudaFuncAttributeMaxDynamicSharedMemorySize, cap);
+    return e;
 }
 
 }  // namespace s3

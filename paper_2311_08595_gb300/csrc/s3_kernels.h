@@ -129,6 +129,13 @@ cudaError_t launch_edge_bern_f32(const TailEntry *tab, int ntab, int64_t nblocks
                                  const float *x, const EdgeOutArgs &o, const BernArgs &c, cudaStream_t st);
 cudaError_t launch_edge_bern_f64(const TailEntry *tab, int ntab, int64_t nblocks, int lane_elems, int fb_elems,
                                  const double *x, const EdgeOutArgs &o, const BernArgs &c, cudaStream_t st);
+// the biased output mode (o.bias != 0), each in a translation unit of its own
+cudaError_t launch_edge_bern_f32_bias(const TailEntry *tab, int ntab, int64_t nblocks, int lane_elems, int fb_elems,
+                                      const float *x, const EdgeOutArgs &o, const BernArgs &c, cudaStream_t st);
+cudaError_t launch_edge_bern_f64_bias(const TailEntry *tab, int ntab, int64_t nblocks, int lane_elems, int fb_elems,
+                                      const double *x, const EdgeOutArgs &o, const BernArgs &c, cudaStream_t st);
+cudaError_t prepare_edge_bern_f32_bias();
+cudaError_t prepare_edge_bern_f64_bias();
 cudaError_t prepare_edge_bern_f32();
 cudaError_t prepare_edge_bern_f64();
 // One-time per-device set-up (shared-memory limits of the kernels).
@@ -166,6 +173,9 @@ struct ReduceArgs {
 };
 cudaError_t launch_reduce_f32(const ReduceArgs &r, const float *buf, float *y, cudaStream_t st);
 cudaError_t launch_reduce_f64(const ReduceArgs &r, const double *buf, double *y, cudaStream_t st);
+// Warm-start features (12 floats per node, row-major) from the per-(edge, node) records in the
+// slot buffer; r.partial must hold n_pieces * 64 bytes for this call.
+cudaError_t launch_feature_reduce(const ReduceArgs &r, const unsigned long long *rec, float *feat, cudaStream_t st);
 
 // y[v] += comp[v] (FP32 atomic mode), v < n
 cudaError_t launch_add_comp(float *y, const float *comp, int64_t n, const int32_t *skip, cudaStream_t st);

@@ -3,10 +3,12 @@
 //
 // Features of node v (all log1p-scaled): degree; mean and max size of the
 // edges containing v; an 8-bin histogram of those sizes (bins log-spaced on
-// [2, N]); the sum over v's edges of the other members' degrees.  They are
-// gathered edge by edge with integer atomics (exact, so the result does not
-// depend on scheduling).  The network predicts log x*_v minus its mean over the
-// graph; the warm start is exp(prediction), normalised to 1-norm 1.
+// [2, N]); the sum over v's edges of the other members' degrees.  Each edge writes
+// one integer record per member into the member's slot of the reduce buffer, and the
+// segmented reduce (s3_reduce.cu) folds each node's records without atomics (exact
+// integer sums, so the result does not depend on scheduling).  The network predicts
+// log x*_v minus its mean over the graph; the warm start is exp(prediction),
+// normalised to 1-norm 1.
 //
 // Training keeps FP32 master weights and their BF16 copies; the forward pass
 // of training and of inference uses the BF16 copies with FP32 accumulation.
@@ -49,84 +51,248 @@ int size_bin(int s, int N) {
     return b < 0 ? 0 : (b > 7 ? 7 : b);
 }
 
-// One thread per edge of one bucket.  Members of neighbouring edges are often the
-// same node (edges are sorted, hubs first), so the lanes of a warp that target one
-// node combine their updates and one lane issues the atomics (the integer sums are
-// exact in any order).
-__global__ void feature_edge_kernel(EdgeBucketArgs b, int bin, const int64_t *__restrict__ inc_ptr,
-                                    unsigned long long *__restrict__ nbr, unsigned int *__restrict__ size_sum,
-                                    int *__restrict__ size_max, unsigned int *__restrict__ hist) {
-    int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+// Per-(edge, node) records for the features, one thread per edge, all buckets in one
+// launch (block ranges map to buckets, tab[k].block0 ascending; the size-bin of bucket k's
+// edges in tab[k].W): the record of member v of edge e goes to v's slot of the reduce
+// buffer, holding |e| (bits 0-7), its bin (bits 8-10) and D_e - deg v (bits 16-63), D_e the
+// degree sum of e's members.  The segmented reduce then folds each node's records.
+__global__ void feature_record_kernel(const TailEntry *__restrict__ tab, int ntab, const int64_t *__restrict__ inc_ptr,
+                                      unsigned long long *__restrict__ rec) {
+    int k = 0;
+    while (k + 1 < ntab && tab[k + 1].block0 <= (int64_t)blockIdx.x) ++k;
+    const EdgeBucketArgs &b = tab[k].b;
+    const unsigned long long tag = ((unsigned long long)tab[k].W << 8) | (unsigned long long)b.s;
+    int64_t e = ((int64_t)blockIdx.x - tab[k].block0) * blockDim.x + threadIdx.x;
     if (e >= b.m) return;
     const int s = b.s;
     unsigned long long D = 0;
     for (int i = 0; i < s; ++i) {
-        int v = b.ids[(int64_t)i * b.ld + e];
-        D += (unsigned long long)(inc_ptr[v + 1] - inc_ptr[v]);
+        const int v = __ldg(b.ids + (int64_t)i * b.ld + e);
+        D += (unsigned long long)(__ldg(inc_ptr + v + 1) - __ldg(inc_ptr + v));
     }
-    const unsigned act = __activemask();
-    const int lane = threadIdx.x & 31;
     for (int i = 0; i < s; ++i) {
-        const int v = b.ids[(int64_t)i * b.ld + e];
-        const unsigned long long dv = (unsigned long long)(inc_ptr[v + 1] - inc_ptr[v]);
-        const unsigned grp = __match_any_sync(act, v);
-        unsigned long long acc = 0;
-        for (unsigned mm = grp; mm; mm &= mm - 1) acc += __shfl_sync(grp, D - dv, __ffs(mm) - 1);
-        if (lane == __ffs(grp) - 1) {
-            const unsigned cnt = (unsigned)__popc(grp);
-            atomicAdd(nbr + v, acc);
-            atomicAdd(size_sum + v, cnt * (unsigned int)s);
-            atomicMax(size_max + v, s);
-            atomicAdd(hist + (int64_t)v * 8 + bin, cnt);
-        }
+        const int v = __ldg(b.ids + (int64_t)i * b.ld + e);
+        const unsigned long long dv = (unsigned long long)(__ldg(inc_ptr + v + 1) - __ldg(inc_ptr + v));
+        rec[__ldg(b.slot + (int64_t)i * b.ld + e)] = ((D - dv) << 16) | tag;
     }
-}
-
-__global__ void feature_finalize_kernel(int64_t n, const int64_t *__restrict__ inc_ptr,
-                                        const unsigned long long *__restrict__ nbr,
-                                        const unsigned int *__restrict__ size_sum, const int *__restrict__ size_max,
-                                        const unsigned int *__restrict__ hist, float *__restrict__ feat) {
-    int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (v >= n) return;
-    const double d = (double)(inc_ptr[v + 1] - inc_ptr[v]);
-    float *f = feat + v * F;
-    f[0] = (float)log1p(d);
-    f[1] = (float)log1p(d > 0 ? (double)size_sum[v] / d : 0.0);
-    f[2] = (float)log1p((double)size_max[v]);
-    for (int k = 0; k < 8; ++k) f[3 + k] = (float)log1p((double)hist[v * 8 + k]);
-    f[11] = (float)log1p((double)nbr[v]);
 }
 
 // ---------------------------------------------------------- inference ---
 
-// out[v] = W3 relu(W2 relu(W1 f_v + b1) + b2) + b3, BF16 weights, FP32 accumulation
-__global__ void __launch_bounds__(128) mlp_forward_kernel(const __nv_bfloat16 *__restrict__ wbf,
-                                                          const float *__restrict__ feat, int64_t n,
-                                                          float *__restrict__ out) {
-    __shared__ float w[NP];
-    for (int i = threadIdx.x; i < NP; i += blockDim.x) w[i] = __bfloat162float(wbf[i]);
+// out[v] = W3 relu(W2 relu(W1 f_v + b1) + b2) + b3 with the BF16 weights, one tile of
+// 128 nodes per CTA (4 warps, one node per thread).  Layer 1 (12 -> 64) and the output
+// layer run on the FP32 units.  Layer 2 (64 x 64, 83 % of the multiply-adds) runs on the
+// tensor cores: D[128 x 64] = A[128 x 64] B^T with B = W2 (BF16, K-major) and A = h1 split
+// into two BF16 terms, hi = bf16(h1) and lo = bf16(h1 - hi), so that the FP32 accumulation
+// of hi W2^T + lo W2^T equals h1 W2^T to about 2^-17 relative (W2 is exactly BF16).  Eight
+// tcgen05.mma (kind::f16, M = 128, N = 64, K = 16 each) accumulate into 64 TMEM columns,
+// read back with tcgen05.ld for the epilogue.
+//
+// Operands in shared memory use the 128-byte-swizzled K-major layout: one 128-byte row
+// per matrix row (64 BF16), 8-row atoms of 1 KB, the 16-byte chunk c of row r stored at
+// chunk c ^ (r % 8).  Descriptor: stride between 8-row groups 1024 B; each K step of 16
+// advances the start address by 32 B inside the atom.
+constexpr int kTcRows = 128;                       // nodes per CTA (the MMA's M)
+constexpr int kTcCols = 64;                        // TMEM columns (the MMA's N; FP32 accumulators)
+constexpr uint32_t kTcIdesc = (1u << 4)            // D: FP32
+                              | (1u << 7)          // A: BF16
+                              | (1u << 10)         // B: BF16
+                              | ((uint32_t)(H >> 3) << 17)        // N = 64
+                              | ((uint32_t)(kTcRows >> 4) << 24); // M = 128 (A and B K-major)
+// dynamic shared memory: A_hi, A_lo (16 KB each), B (8 KB), then FP32 copies of W1, b1, b2,
+// W3, b3 and the mbarrier / TMEM address words
+constexpr size_t kTcA = (size_t)kTcRows * 128, kTcB = (size_t)H * 128;
+constexpr int kTcSmall = H * F + H + H + H + 1;
+constexpr size_t kTcSmem = 1024 /* alignment slack */ + 2 * kTcA + kTcB + sizeof(float) * kTcSmall + 32;
+constexpr long long kTcWaitPolls = 1ll << 22;      // bound on the MMA-completion wait
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+// shared-memory matrix descriptor: 128-byte swizzle, K-major, 8-row groups 1024 B apart
+__device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
+    return (uint64_t)((saddr & 0x3FFFFu) >> 4)   // start address
+           | ((uint64_t)1 << 16)                 // leading-dimension offset (unused with this swizzle)
+           | ((uint64_t)(1024 >> 4) << 32)       // stride-dimension offset
+           | ((uint64_t)1 << 46)                 // descriptor version
+           | ((uint64_t)2 << 61);                // 128-byte swizzle
+}
+
+// byte offset of 16-byte chunk c of row r in a 128-byte-swizzled K-major tile
+__device__ __forceinline__ uint32_t sw128_off(int r, int c) {
+    return (uint32_t)((r >> 3) * 1024 + (r & 7) * 128 + ((c ^ (r & 7)) << 4));
+}
+
+__device__ __forceinline__ uint32_t pack_bf16(float a, float b) {
+    const __nv_bfloat16 x = __float2bfloat16_rn(a), y = __float2bfloat16_rn(b);
+    return (uint32_t)__bfloat16_as_ushort(x) | ((uint32_t)__bfloat16_as_ushort(y) << 16);
+}
+
+__global__ void __launch_bounds__(kTcRows) mlp_forward_tc_kernel(const __nv_bfloat16 *__restrict__ wbf,
+                                                                  const float *__restrict__ feat, int64_t n,
+                                                                  float *__restrict__ out, int vec_feat,
+                                                                  int *__restrict__ err) {
+    extern __shared__ unsigned char smem_raw[];
+    unsigned char *base = reinterpret_cast<unsigned char *>(
+        (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
+    unsigned char *a_hi = base, *a_lo = base + kTcA, *b_w2 = base + 2 * kTcA;
+    float *w1 = reinterpret_cast<float *>(b_w2 + kTcB);   // W1[H][F]
+    float *b1 = w1 + H * F, *b2 = b1 + H, *w3 = b2 + H, *b3 = w3 + H;
+    uint64_t *mbar = reinterpret_cast<uint64_t *>(
+        (reinterpret_cast<uintptr_t>(b3 + 1) + 7) & ~(uintptr_t)7);
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(mbar + 1);
+    const int tid = threadIdx.x, warp = tid >> 5;
+
+    // TMEM: 64 columns, allocated by warp 0
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                     "r"(kTcCols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    if (tid == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(mbar)), "r"(1) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    // W2 into the B tile (row n = output unit n, 64 BF16 = 8 chunks), the rest as FP32
+    {
+        const uint4 *src = reinterpret_cast<const uint4 *>(wbf + OW2);
+        for (int i = tid; i < H * 8; i += kTcRows) {
+            const int r = i >> 3, c = i & 7;
+            *reinterpret_cast<uint4 *>(b_w2 + sw128_off(r, c)) = __ldg(src + i);
+        }
+        for (int i = tid; i < H * F + H; i += kTcRows) w1[i] = __bfloat162float(wbf[OW1 + i]);  // W1 then b1
+        for (int i = tid; i < H; i += kTcRows) {
+            b2[i] = __bfloat162float(wbf[OB2 + i]);
+            w3[i] = __bfloat162float(wbf[OW3 + i]);
+        }
+        if (tid == 0) *b3 = __bfloat162float(wbf[OB3]);
+    }
     __syncthreads();
-    int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (v >= n) return;
+
+    // layer 1 on the FP32 units: node v = this thread's row; h1 split into the A tiles
+    const int64_t v = (int64_t)blockIdx.x * kTcRows + tid;
     float f[F];
+    if (v < n && vec_feat) {
+        const float4 *fp = reinterpret_cast<const float4 *>(feat + v * F);
 #pragma unroll
-    for (int i = 0; i < F; ++i) f[i] = feat[v * F + i];
-    float h1[H];
+        for (int q = 0; q < F / 4; ++q) {
+            const float4 t = __ldg(fp + q);
+            f[4 * q] = t.x;
+            f[4 * q + 1] = t.y;
+            f[4 * q + 2] = t.z;
+            f[4 * q + 3] = t.w;
+        }
+    } else {
 #pragma unroll
-    for (int j = 0; j < H; ++j) {
-        float acc = w[OB1 + j];
-#pragma unroll
-        for (int i = 0; i < F; ++i) acc = fmaf(w[OW1 + j * F + i], f[i], acc);
-        h1[j] = fmaxf(acc, 0.f);
+        for (int i = 0; i < F; ++i) f[i] = v < n ? __ldg(feat + v * F + i) : 0.f;
     }
-    float y = w[OB3];
-    for (int j = 0; j < H; ++j) {
-        float acc = w[OB2 + j];
+#pragma unroll 1
+    for (int c = 0; c < H / 8; ++c) {
+        float h[8];
 #pragma unroll
-        for (int k = 0; k < H; ++k) acc = fmaf(w[OW2 + j * H + k], h1[k], acc);
-        y = fmaf(w[OW3 + j], fmaxf(acc, 0.f), y);
+        for (int jj = 0; jj < 8; ++jj) {
+            const int j = 8 * c + jj;
+            float acc = b1[j];
+#pragma unroll
+            for (int i = 0; i < F; i += 4) {
+                const float4 q = *reinterpret_cast<const float4 *>(w1 + j * F + i);
+                acc = fmaf(q.x, f[i], acc);
+                acc = fmaf(q.y, f[i + 1], acc);
+                acc = fmaf(q.z, f[i + 2], acc);
+                acc = fmaf(q.w, f[i + 3], acc);
+            }
+            h[jj] = fmaxf(acc, 0.f);
+        }
+        uint32_t hi[4], lo[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const float x0 = h[2 * q], x1 = h[2 * q + 1];
+            hi[q] = pack_bf16(x0, x1);
+            const float r0 = x0 - __bfloat162float(__ushort_as_bfloat16((unsigned short)(hi[q] & 0xffffu)));
+            const float r1 = x1 - __bfloat162float(__ushort_as_bfloat16((unsigned short)(hi[q] >> 16)));
+            lo[q] = pack_bf16(r0, r1);
+        }
+        const uint32_t off = sw128_off(tid, c);
+        *reinterpret_cast<uint4 *>(a_hi + off) = make_uint4(hi[0], hi[1], hi[2], hi[3]);
+        *reinterpret_cast<uint4 *>(a_lo + off) = make_uint4(lo[0], lo[1], lo[2], lo[3]);
     }
-    out[v] = y;
+    // the A tiles (generic-proxy stores) become visible to the tensor cores (async proxy)
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = *tmem_slot;
+
+    // layer 2 on the tensor cores: one thread issues the eight MMAs and commits them to the mbarrier
+    if (tid == 0) {
+        const uint32_t sa[2] = {smem_u32(a_hi), smem_u32(a_lo)};
+        const uint32_t sb = smem_u32(b_w2);
+#pragma unroll
+        for (int part = 0; part < 2; ++part) {
+#pragma unroll
+            for (int k = 0; k < H / 16; ++k) {
+                const uint64_t da = sw128_desc(sa[part] + 32u * k);
+                const uint64_t db = sw128_desc(sb + 32u * k);
+                const uint32_t accum = (part | k) ? 1u : 0u;
+                asm volatile(
+                    "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+                    "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem),
+                    "l"(da), "l"(db), "r"(kTcIdesc), "r"(accum)
+                    : "memory");
+            }
+        }
+        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                         smem_u32(mbar))
+                     : "memory");
+    }
+    // wait for the MMAs (bounded: on timeout flag the error, skip the epilogue)
+    bool done = false;
+    for (long long it = 0; it < kTcWaitPolls; ++it) {
+        uint32_t ok;
+        asm volatile(
+            "{\n\t.reg .pred P;\n\tmbarrier.try_wait.parity.shared::cta.b64 P, [%1], %2;\n\t"
+            "selp.b32 %0, 1, 0, P;\n\t}"
+            : "=r"(ok)
+            : "r"(smem_u32(mbar)), "r"(0)
+            : "memory");
+        if (ok) {
+            done = true;
+            break;
+        }
+        if (it > 64) __nanosleep(64);
+    }
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    if (__all_sync(0xffffffffu, done)) {
+        // epilogue: this warp's 32 TMEM lanes (= rows), 16 columns at a time
+        float y = *b3;
+#pragma unroll
+        for (int c0 = 0; c0 < H; c0 += 16) {
+            uint32_t r[16];
+            const uint32_t ta = tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)c0;
+            asm volatile(
+                "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, "
+                "%13, %14, %15}, [%16];"
+                : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+                  "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
+                  "=r"(r[15])
+                : "r"(ta)
+                : "memory");
+            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+            for (int j = 0; j < 16; ++j) y = fmaf(w3[c0 + j], fmaxf(__uint_as_float(r[j]) + b2[c0 + j], 0.f), y);
+        }
+        if (v < n) out[v] = y;
+    } else if ((tid & 31) == 0) {
+        atomicExch(err, 1);
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 0) {
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTcCols) : "memory");
+    }
 }
 
 // ----------------------------------------------------------- training ---
@@ -255,7 +421,8 @@ __global__ void warm_exp_kernel(const float *__restrict__ out, int64_t n, double
     __shared__ double sh[256 / 32];
     double acc = 0.0;
     for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
-        double e = exp((double)out[v] - shift);
+        // FP32 exponential: x0 is a start vector, whose precision does not decide the result
+        const double e = (double)expf(out[v] - (float)shift);
         x0[v] = e;
         acc += e;
     }
@@ -343,6 +510,7 @@ struct s3_mlp_s {
     double *lpart = nullptr;
     int64_t part_cap = 0;          // blocks the partial arrays hold
     int64_t step = 0;
+    int *d_err = nullptr;          // set by a tensor-core wait that ran out
     std::vector<void *> allocations;
 };
 
@@ -356,6 +524,16 @@ s3_status mlp_alloc(s3_mlp_s *m, void **p, size_t bytes) {
     }
     m->allocations.push_back(*p);
     return S3_OK;
+}
+
+// the flag a tensor-core wait sets when it runs out: read (synchronising `st`), cleared, reported
+s3_status take_error(s3_mlp_s *m, cudaStream_t st) {
+    int h = 0;
+    S3_CUDA(cudaMemcpyAsync(&h, m->d_err, sizeof(int), cudaMemcpyDeviceToHost, st));
+    S3_CUDA(cudaStreamSynchronize(st));
+    if (!h) return S3_OK;
+    S3_CUDA(cudaMemsetAsync(m->d_err, 0, sizeof(int), st));
+    return fail(S3_ETIMEOUT, "a tensor-core completion wait of the MLP forward pass ran out");
 }
 
 s3_status ensure_parts(s3_mlp_s *m, int64_t blocks) {
@@ -394,33 +572,49 @@ s3_status s3_features(s3_graph_t g, float *feat, void *stream) {
     if (!g || !feat) return fail(S3_EINVAL, "NULL argument");
     DeviceGuard guard(g->device);
     cudaStream_t st = (cudaStream_t)stream;
-    if (!g->d_feat_scratch) {
-        // nbr (u64), size_sum (u32), size_max (i32), hist (8 x u32): 48 bytes per node
-        s3_status s = dev_alloc(g, &g->d_feat_scratch, (size_t)g->n * 12 + 8);
+    if (!g->d_feat_scratch && g->n_pieces > 0) {
+        // per-piece partial accumulators of the hub nodes (64 bytes each)
+        s3_status s = dev_alloc(g, &g->d_feat_scratch, (size_t)g->n_pieces * 16);
         if (s != S3_OK) return s;
     }
-    char *base = reinterpret_cast<char *>(g->d_feat_scratch);
-    auto *nbr = reinterpret_cast<unsigned long long *>(base);
-    auto *ssum = reinterpret_cast<unsigned int *>(base + 8 * (size_t)g->n);
-    auto *smax = reinterpret_cast<int *>(base + 12 * (size_t)g->n);
-    auto *hist = reinterpret_cast<unsigned int *>(base + 16 * (size_t)g->n);
-    S3_CUDA(cudaMemsetAsync(base, 0, 48 * (size_t)g->n, st));
-    for (size_t k = 0; k < g->buckets.size(); ++k) {
-        const HostBucket &hb = g->buckets[k];
-        if (hb.m <= 0) continue;
-        EdgeBucketArgs b{};
-        b.ids = g->d_ids + hb.offset;
-        b.m = hb.m;
-        b.ld = hb.ld;
-        b.s = hb.s;
-        b.N = g->N;
-        feature_edge_kernel<<<(unsigned)((hb.m + 255) / 256), 256, 0, st>>>(b, size_bin(hb.s, g->N), g->d_inc_ptr, nbr,
-                                                                           ssum, smax, hist);
+    if (!g->d_feat_tab) {
+        // one table of the buckets for the fused launch (built once per handle)
+        std::vector<TailEntry> tab;
+        int64_t blocks = 0;
+        for (size_t k = 0; k < g->buckets.size(); ++k) {
+            const HostBucket &hb = g->buckets[k];
+            if (hb.m <= 0) continue;
+            TailEntry t{};
+            t.b.ids = g->d_ids + hb.offset;
+            t.b.slot = g->d_slot + hb.offset;
+            t.b.m = hb.m;
+            t.b.ld = hb.ld;
+            t.b.s = hb.s;
+            t.b.N = g->N;
+            t.W = size_bin(hb.s, g->N);
+            t.block0 = blocks;
+            blocks += (hb.m + 255) / 256;
+            tab.push_back(t);
+        }
+        if (!tab.empty()) {
+            TailEntry *d = nullptr;
+            s3_status s = dev_alloc(g, &d, tab.size());
+            if (s != S3_OK) return s;
+            S3_CUDA(cudaMemcpy(d, tab.data(), sizeof(TailEntry) * tab.size(), cudaMemcpyHostToDevice));
+            g->d_feat_tab = d;
+        }
+        g->n_feat_tab = (int32_t)tab.size();
+        g->feat_blocks = blocks;
+    }
+    auto *rec = reinterpret_cast<unsigned long long *>(g->d_buf);
+    if (g->n_feat_tab > 0) {
+        feature_record_kernel<<<(unsigned)g->feat_blocks, 256, 0, st>>>(g->d_feat_tab, g->n_feat_tab, g->d_inc_ptr,
+                                                                        rec);
         S3_CUDA(cudaGetLastError());
     }
-    feature_finalize_kernel<<<(unsigned)((g->n + 255) / 256), 256, 0, st>>>(g->n, g->d_inc_ptr, nbr, ssum, smax, hist,
-                                                                           feat);
-    S3_CUDA(cudaGetLastError());
+    ReduceArgs r = reduce_args(g, nullptr);
+    r.partial = g->d_feat_scratch;
+    S3_CUDA(launch_feature_reduce(r, rec, feat, st));
     return S3_OK;
 }
 
@@ -449,11 +643,13 @@ s3_status s3_mlp_create(const float *params, uint64_t seed, s3_mlp_t *out) {
     m->grad = reinterpret_cast<float *>(p);
     if ((s = mlp_alloc(m, &p, sizeof(double))) != S3_OK) return bail(s);
     m->loss = reinterpret_cast<double *>(p);
+    if ((s = mlp_alloc(m, &p, sizeof(int))) != S3_OK) return bail(s);
+    m->d_err = reinterpret_cast<int *>(p);
     std::vector<float> h(NP);
     for (int i = 0; i < NP; ++i) h[i] = params ? params[i] : init_value(seed, i);
     if (cudaMemcpy(m->wf, h.data(), sizeof(float) * NP, cudaMemcpyHostToDevice) != cudaSuccess ||
         cudaMemset(m->m1, 0, sizeof(float) * NP) != cudaSuccess ||
-        cudaMemset(m->m2, 0, sizeof(float) * NP) != cudaSuccess)
+        cudaMemset(m->m2, 0, sizeof(float) * NP) != cudaSuccess || cudaMemset(m->d_err, 0, sizeof(int)) != cudaSuccess)
         return bail(cuda_fail(cudaGetLastError(), "cudaMemcpy"));
     if (cudaFuncSetAttribute(mlp_train_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTrainSmem) !=
         cudaSuccess)
@@ -468,6 +664,8 @@ s3_status s3_mlp_get_params(s3_mlp_t m, float *params, int32_t bf16) {
     if (!m || !params) return fail(S3_EINVAL, "NULL argument");
     DeviceGuard guard(m->device);
     S3_CUDA(cudaDeviceSynchronize());
+    s3_status es = take_error(m, nullptr);
+    if (es != S3_OK) return es;
     if (!bf16) {
         S3_CUDA(cudaMemcpy(params, m->wf, sizeof(float) * NP, cudaMemcpyDeviceToHost));
         return S3_OK;
@@ -482,7 +680,11 @@ s3_status s3_mlp_forward(s3_mlp_t m, const float *feat, int64_t n, float *out, v
     if (!m || !feat || !out || n < 0) return fail(S3_EINVAL, "bad argument");
     if (n == 0) return S3_OK;
     DeviceGuard guard(m->device);
-    mlp_forward_kernel<<<(unsigned)((n + 127) / 128), 128, 0, (cudaStream_t)stream>>>(m->wbf, feat, n, out);
+    const int64_t blocks = (n + kTcRows - 1) / kTcRows;
+    if (blocks > INT32_MAX) return fail(S3_EINVAL, "too many nodes");
+    const int vec = (reinterpret_cast<uintptr_t>(feat) & 15) == 0;
+    mlp_forward_tc_kernel<<<(unsigned)blocks, kTcRows, kTcSmem, (cudaStream_t)stream>>>(m->wbf, feat, n, out, vec,
+                                                                                          m->d_err);
     S3_CUDA(cudaGetLastError());
     return S3_OK;
 }
@@ -539,7 +741,8 @@ s3_status s3_warmstart(s3_graph_t g, s3_mlp_t m, double *x0, void *stream) {
     S3_CUDA(cudaGetLastError());
     float hmx[256];
     S3_CUDA(cudaMemcpyAsync(hmx, mx, sizeof(float) * nb, cudaMemcpyDeviceToHost, st));
-    S3_CUDA(cudaStreamSynchronize(st));
+    s = take_error(m, st);   // synchronises st
+    if (s != S3_OK) return s;
     float shift = -INFINITY;
     for (int i = 0; i < nb; ++i) shift = std::max(shift, hmx[i]);
     if (!std::isfinite(shift)) return fail(S3_ERANGE, "warm-start prediction is not finite");

@@ -92,6 +92,85 @@ __device__ __forceinline__ void load_partial(const void *p, int64_t i, AccD &a) 
     a.s += __ldcg(reinterpret_cast<const double *>(p) + i);
 }
 
+// Per-node warm-start features from per-(edge, node) records (s3_mlp.cu writes them):
+// bits 0-7 the edge size s, bits 8-10 its histogram bin, bits 16-63 the sum of the
+// other members' degrees; 0 is no record (a padded load).  Integer sums: exact.
+struct __align__(8) FeatAcc {
+    unsigned h[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    unsigned smax = 0;
+    unsigned long long ssum = 0, nbr = 0;
+    __device__ void add(unsigned long long rec) {
+        const unsigned sz = (unsigned)(rec & 0xffu), b = (unsigned)(rec >> 8) & 7u;
+        const unsigned one = rec != 0ull;
+#pragma unroll
+        for (int k = 0; k < 8; ++k) h[k] += (b == (unsigned)k) ? one : 0u;
+        smax = max(smax, sz);
+        ssum += sz;
+        nbr += rec >> 16;
+    }
+    __device__ void merge(const FeatAcc &o) {
+#pragma unroll
+        for (int k = 0; k < 8; ++k) h[k] += o.h[k];
+        smax = max(smax, o.smax);
+        ssum += o.ssum;
+        nbr += o.nbr;
+    }
+};
+
+__device__ __forceinline__ FeatAcc shfl_down_acc(const FeatAcc &a, int d) {
+    FeatAcc r;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) r.h[k] = __shfl_down_sync(0xffffffffu, a.h[k], d);
+    r.smax = __shfl_down_sync(0xffffffffu, a.smax, d);
+    r.ssum = __shfl_down_sync(0xffffffffu, a.ssum, d);
+    r.nbr = __shfl_down_sync(0xffffffffu, a.nbr, d);
+    return r;
+}
+
+__device__ __forceinline__ void store_partial(void *p, int64_t i, const FeatAcc &a) {
+    reinterpret_cast<FeatAcc *>(p)[i] = a;
+}
+__device__ __forceinline__ void load_partial(const void *p, int64_t i, FeatAcc &a) {
+    const FeatAcc *q = reinterpret_cast<const FeatAcc *>(p) + i;
+    FeatAcc t;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) t.h[k] = __ldcg(&q->h[k]);
+    t.smax = __ldcg(&q->smax);
+    t.ssum = __ldcg(&q->ssum);
+    t.nbr = __ldcg(&q->nbr);
+    a.merge(t);
+}
+
+// the 12 features of node v (row v of feat), log1p-scaled in FP32: degree; mean and max
+// size of its edges; the 8-bin size histogram; the other members' degree sum
+struct FeatSink {
+    float *feat;
+    bool vec;   // feat 16-byte aligned: rows written as three float4
+    __device__ void put(int v, const FeatAcc &a) const {
+        unsigned d = 0;
+#pragma unroll
+        for (int k = 0; k < 8; ++k) d += a.h[k];
+        float f[12];
+        const float df = (float)d;
+        f[0] = log1pf(df);
+        f[1] = log1pf(d ? (float)a.ssum / df : 0.f);
+        f[2] = log1pf((float)a.smax);
+#pragma unroll
+        for (int k = 0; k < 8; ++k) f[3 + k] = log1pf((float)a.h[k]);
+        f[11] = log1pf((float)a.nbr);
+        static_assert(sizeof(FeatAcc) <= 64, "feature partials hold 64 bytes");
+        float *row = feat + (int64_t)v * 12;
+        if (vec) {
+#pragma unroll
+            for (int q = 0; q < 3; ++q)
+                reinterpret_cast<float4 *>(row)[q] = make_float4(f[4 * q], f[4 * q + 1], f[4 * q + 2], f[4 * q + 3]);
+        } else {
+#pragma unroll
+            for (int k = 0; k < 12; ++k) row[k] = f[k];
+        }
+    }
+};
+
 constexpr int kRedThreads = 256;
 
 // Eight loads in flight per thread, predicated at the end of a segment (a
@@ -102,11 +181,12 @@ constexpr int kRedUnroll = 8;
 // Blocks [0, n_pieces): one hub piece each (the longest-running blocks start
 // first); then one warp per medium node of degree > 128; then eight lanes per
 // medium node of degree <= 128; then one warp per group of 32 small nodes.
-template <typename T>
-__global__ void __launch_bounds__(kRedThreads) reduce_kernel(ReduceArgs r, const T *__restrict__ buf, T *__restrict__ y,
+// T: the slot values; A: the accumulator (add, merge, a shuffle and a partial-sum store
+// of its own); Sink: writes a node's result (put(node, acc)).
+template <typename T, typename A, typename Sink>
+__global__ void __launch_bounds__(kRedThreads) reduce_kernel(ReduceArgs r, const T *__restrict__ buf, Sink y,
                                                              int64_t nb_med, int64_t nb_med8, int64_t nb_grp) {
     if (r.skip && *r.skip) return;
-    using A = typename AccOf<T>::type;
     constexpr int U = kRedUnroll;
     const int64_t bid = blockIdx.x;
     const int tid = threadIdx.x;
@@ -147,7 +227,7 @@ __global__ void __launch_bounds__(kRedThreads) reduce_kernel(ReduceArgs r, const
             A t;
             for (int q = r.big_piece_ptr[hb] + lane; q < r.big_piece_ptr[hb + 1]; q += 32) load_partial(r.partial, q, t);
             t = warp_reduce(t);
-            if (lane == 0) y[r.big_nodes[hb]] = (T)t.value();
+            if (lane == 0) y.put(r.big_nodes[hb], t);
         }
     } else if (bid < r.n_pieces + nb_med) {
         const int64_t i = (bid - r.n_pieces) * (kRedThreads / 32) + (tid >> 5);
@@ -164,7 +244,7 @@ __global__ void __launch_bounds__(kRedThreads) reduce_kernel(ReduceArgs r, const
             for (int u = 0; u < U; ++u) a.add(w[u]);  // adding 0 leaves the sum unchanged
         }
         a = warp_reduce(a);
-        if (lane == 0) y[v] = (T)a.value();
+        if (lane == 0) y.put(v, a);
     } else if (bid < r.n_pieces + nb_med + nb_med8) {
         // eight lanes per node; lanes of a missing node read nothing but join the shuffles
         const int64_t i = (bid - r.n_pieces - nb_med) * (kRedThreads / 8) + (tid >> 3);
@@ -181,7 +261,7 @@ __global__ void __launch_bounds__(kRedThreads) reduce_kernel(ReduceArgs r, const
             for (int u = 0; u < U; ++u) a.add(w[u]);
         }
         a = group8_reduce(a);
-        if (has && sl == 0) y[r.med8_nodes[i]] = (T)a.value();
+        if (has && sl == 0) y.put(r.med8_nodes[i], a);
     } else {
         const int64_t gi = (bid - r.n_pieces - nb_med - nb_med8) * (kRedThreads / 32) + (tid >> 5);
         if (gi >= r.n_grp) return;
@@ -196,18 +276,25 @@ __global__ void __launch_bounds__(kRedThreads) reduce_kernel(ReduceArgs r, const
 #pragma unroll
             for (int u = 0; u < U; ++u) a.add(w[u]);
         }
-        if (node >= 0) y[node] = (T)a.value();
+        if (node >= 0) y.put(node, a);
     }
 }
 
+// y_v = the sum of node v's values
 template <typename T>
-cudaError_t launch_reduce_t(const ReduceArgs &r, const T *buf, T *y, cudaStream_t st) {
+struct SumSink {
+    T *y;
+    __device__ void put(int v, const typename AccOf<T>::type &a) const { y[v] = (T)a.value(); }
+};
+
+template <typename T, typename A, typename Sink>
+cudaError_t launch_reduce_t(const ReduceArgs &r, const T *buf, Sink y, cudaStream_t st) {
     int64_t nb_grp = (r.n_grp + (kRedThreads / 32) - 1) / (kRedThreads / 32);
     int64_t nb_med = (r.n_med + (kRedThreads / 32) - 1) / (kRedThreads / 32);
     int64_t nb_med8 = (r.n_med8 + (kRedThreads / 8) - 1) / (kRedThreads / 8);
     int64_t grid = nb_grp + nb_med + nb_med8 + r.n_pieces;
     if (grid > 0) {
-        reduce_kernel<T><<<(unsigned)grid, kRedThreads, 0, st>>>(r, buf, y, nb_med, nb_med8, nb_grp);
+        reduce_kernel<T, A, Sink><<<(unsigned)grid, kRedThreads, 0, st>>>(r, buf, y, nb_med, nb_med8, nb_grp);
         return cudaGetLastError();
     }
     return cudaSuccess;
@@ -222,10 +309,14 @@ __global__ void add_comp_kernel(float *y, const float *comp, int64_t n, const in
 }  // namespace
 
 cudaError_t launch_reduce_f32(const ReduceArgs &r, const float *buf, float *y, cudaStream_t st) {
-    return launch_reduce_t<float>(r, buf, y, st);
+    return launch_reduce_t<float, AccF>(r, buf, SumSink<float>{y}, st);
 }
 cudaError_t launch_reduce_f64(const ReduceArgs &r, const double *buf, double *y, cudaStream_t st) {
-    return launch_reduce_t<double>(r, buf, y, st);
+    return launch_reduce_t<double, AccD>(r, buf, SumSink<double>{y}, st);
+}
+cudaError_t launch_feature_reduce(const ReduceArgs &r, const unsigned long long *rec, float *feat, cudaStream_t st) {
+    return launch_reduce_t<unsigned long long, FeatAcc>(
+        r, rec, FeatSink{feat, (reinterpret_cast<uintptr_t>(feat) & 15) == 0}, st);
 }
 cudaError_t launch_add_comp(float *y, const float *comp, int64_t n, const int32_t *skip, cudaStream_t st) {
     if (n <= 0) return cudaSuccess;

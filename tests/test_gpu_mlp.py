@@ -26,6 +26,26 @@ def test_features_match_oracle(which):
     assert np.allclose(f, want, rtol=1e-6, atol=1e-6)
 
 
+def test_features_every_degree_class():
+    # a hub of degree 5000 (cut into pieces), nodes of degree 250 (a warp each) and 100
+    # (eight lanes each), many of degree <= 32 (sliced-ELL groups) and isolated nodes
+    import paper_2311_08595_gb300 as s3
+    edges = []
+    for i in range(5000):
+        e = [0, 1 + i % 300, 301 + i % 50]
+        if i % 2 == 0:
+            e.append(351 + i % 10)
+        e += [400 + (7 * i + j) % 3000 for j in range(i % 5)]
+        edges.append(tuple(dict.fromkeys(e)))
+    hg = s3synth.from_edges(3500, edges, rank=9)
+    g = s3.s3_build_format(hg.n, hg.edge_ptr, hg.members, rank=hg.rank)
+    f = s3.s3_features(g).cpu().numpy().astype(np.float64)
+    want = mlp.features(hg)
+    assert np.allclose(f, want, rtol=1e-6, atol=1e-6)
+    assert f[0, 0] == pytest.approx(np.log1p(5000), rel=1e-6)
+    assert np.all(f[3400:] == 0)
+
+
 def test_forward_loss_gradient_and_adam_match_oracle():
     import paper_2311_08595_gb300 as s3
     rng = np.random.default_rng(1)
@@ -40,6 +60,12 @@ def test_forward_loss_gradient_and_adam_match_oracle():
     y = s3.s3_mlp_forward(m, fd).cpu().numpy()
     yo, _ = mlp.forward(pb, feat.astype(np.float64))
     assert np.max(np.abs(y - yo)) <= 1e-4 * max(1.0, np.max(np.abs(yo)))
+    # features at an address that is not 16-byte aligned (scalar loads): the same outputs
+    import torch
+    shifted = torch.empty(n * mlp.F + 1, dtype=torch.float32, device="cuda")[1:]
+    shifted.copy_(fd.reshape(-1))
+    y2 = s3.s3_mlp_forward(m, shifted.view(n, mlp.F)).cpu().numpy()
+    assert np.array_equal(y, y2)
     loss, grad = s3.s3_mlp_loss_grad(m, fd, td)
     lo, go = mlp.loss_and_grad(pb, feat.astype(np.float64), tgt.astype(np.float64))
     assert abs(loss - lo) <= 1e-5 * lo

@@ -42,6 +42,10 @@ def test_version_and_status_strings(s3):
     assert s3.s3_version() == 1
     from paper_2311_08595_gb300 import _lib
     assert _lib.status_name(0) == "S3_OK" and _lib.status_name(4) == "S3_ENOCONV"
+    # every status of the header has its name, in the header's order
+    names = ["S3_OK", "S3_EINVAL", "S3_ENOMEM", "S3_ECUDA", "S3_ENOCONV", "S3_ETIMEOUT", "S3_ERANGE", "S3_ENOTSUP"]
+    assert [_lib.status_name(i) for i in range(8)] == names
+    assert [getattr(_lib, k) for k in names] == list(range(8))
 
 
 def test_inspect_fig1_matches_fig2_counts(s3):
