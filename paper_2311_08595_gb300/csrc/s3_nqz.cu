@@ -37,6 +37,23 @@ constexpr int kNqzBlocks = 592;   // 4 x 148..152 SMs; fixed so sums are reprodu
 // flags: [0] done, [1] iterations, [2] hit max_iter, [3] range trouble, [4] block counter
 enum { F_DONE = 0, F_ITERS = 1, F_MAXED = 2, F_RANGE = 3 };
 
+// 1/y for y > 0 to FP32 accuracy (relative error below 2^-22), as a double: the FP32
+// reciprocal of y's mantissa, scaled back by y's exponent (exact), so no range is lost.
+__device__ __forceinline__ double rcp_seed(double y) {
+    const int ey = Arith<double>::expo(y);
+    const float my = (float)(y * Arith<double>::pow2(-ey));   // [0.5, 1)
+    return (double)__frcp_rn(my) * Arith<double>::pow2(-ey);
+}
+
+// a / y for y > 0: the FP32-accurate quotient q = a r0 (r0 = rcp_seed(y)) and one correction
+// with the exact residual a - q y (an FMA), which leaves a relative error of about 2^-44 plus
+// the roundings -- the FP64 units' division sequence costs several times more.
+__device__ __forceinline__ double div_refined(double a, double y) {
+    const double r0 = rcp_seed(y);
+    const double q = a * r0;
+    return fma(fma(-q, y, a), r0, q);
+}
+
 // r = a^(1/k) for a > 0: FP32 guess then one Newton step in FP64.
 __device__ __forceinline__ double root_k(double a, int k) {
     if (!(a > 0.0)) return 0.0;
@@ -54,7 +71,8 @@ __device__ __forceinline__ double root_k(double a, int k) {
         if (e & 1) rk1 *= base;
         base *= base;
     }
-    r = r - (rk1 * r - b) / ((double)k * rk1);
+    // the step's own size is ~1e-7 r, so its divisor needs FP32 accuracy only
+    r = r - fma(rk1, r, -b) * rcp_seed((double)k * rk1);
     return r * Arith<double>::pow2(q);
 }
 
@@ -128,7 +146,7 @@ __global__ void __launch_bounds__(kNqzThreads) nqz_after_kernel(const T *__restr
                 if (q & 1) pk *= base;
                 base *= base;
             }
-            const double ratio = z / pk;
+            const double ratio = div_refined(z, pk);
             bad |= !isfinite(ratio) || !(ratio > 0.0);
             lo = fmin(lo, ratio);
             hi = fmax(hi, ratio);
