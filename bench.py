@@ -350,15 +350,19 @@ def run_gpu(args):
     pclocks = pclk.summary()
     achieved_tflops = flops / (edge_ms * 1e-3) / 1e12
     bytes_call = hbm_bytes(nnz, n)
-    # DRAM traffic of the edge kernels of one call, from the committed ncu capture -- only while
+    # DRAM traffic of one Bernoulli launch, from the committed ncu capture of that kernel on a
+    # smaller case of the same recipe, scaled by the members the launch processes -- only while
     # the kernel sources are the ones it was taken with
-    traffic = None
-    tp = os.path.join(ROOT, "profiles", "edge_kernels_traffic.json")
+    traffic, traffic_note = None, None
+    bern_members = int(sum(info["edges_per_size"][s_] * s_ for s_ in bern["f32"]))
+    tp = os.path.join(ROOT, "profiles", "edge_bern_traffic.json")
     if os.path.exists(tp):
         try:
             tj = json.load(open(tp))
             if tj.get("csrc_digest") == csrc_digest():
-                traffic = tj.get("bytes_per_call")
+                traffic = tj["bytes_per_member"] * bern_members
+                traffic_note = ("dram__bytes_read.sum + dram__bytes_write.sum of edge_bern_kernel<float> on "
+                                + tj["workload"] + f" ({tj['members']} members), scaled to {bern_members} members")
         except Exception:
             traffic = None
     out = {
@@ -375,7 +379,8 @@ def run_gpu(args):
                      "achieved": bflops / (bern_ms * 1e-3) / 1e12 if bern_ms > 0 else None,
                      "peak": p32["tflops"], "unit": "TFLOP/s",
                      "frac": bflops / (bern_ms * 1e-3) / 1e12 / p32["tflops"] if bern_ms > 0 else None,
-                     "traffic": traffic,
+                     "traffic": traffic, "traffic_note": traffic_note,
+                     "algorithmic_bytes_per_launch": bern_members * 8 + n * 4,
                      "peak_note": "of measured: FP32 FMA-chain probe (s3_fma_peak) on this device, "
                                   f"{p32['sm_count']} SMs, median SM clock {pclocks['sm_mhz']} MHz during the probe",
                      "algorithmic_flops_per_launch": bflops, "launch_ms": bern_ms,
@@ -398,12 +403,13 @@ def run_gpu(args):
     }
     # FP64 S^3TTVc (event-timed over 20 calls), with its roofline against the FP64 FMA peak
     x64, y64 = x.double(), torch.empty(n, dtype=torch.float64, device=dev)
-    ms64 = _time_calls(g, x64, y64, 20)
+    with ClockSampler(local) as c64:   # clocks under sustained FP64 load (about 0.2 s)
+        ms64 = _time_calls(g, x64, y64, 100)
     prof64 = [s3.s3_sttsvc_profile(g, x64, y64) for _ in range(3)]
     edge64 = float(np.mean([p["edge_ms"] for p in prof64]))
     flops64, _ = algorithmic_counts(info["edges_per_size"], N, closed["f64"], bern["f64"], "powersum")
-    out["fp64"] = {"value": nnz / (ms64 * 1e-3), "unit": UNIT, "ms_per_call": ms64, "calls_timed": 20,
-                   "fp32_speedup": ms64 / ms,
+    out["fp64"] = {"value": nnz / (ms64 * 1e-3), "unit": UNIT, "ms_per_call": ms64, "calls_timed": 100,
+                   "fp32_speedup": ms64 / ms, "clocks": c64.summary(),
                    "roofline": {"bound": "alu", "achieved": flops64 / (edge64 * 1e-3) / 1e12, "peak": p64["tflops"],
                                 "unit": "TFLOP/s", "frac": flops64 / (edge64 * 1e-3) / 1e12 / p64["tflops"],
                                 "edge_ms": edge64, "closed_form_sizes": closed["f64"], "bernoulli_sizes": bern["f64"],
@@ -430,6 +436,7 @@ def run_gpu(args):
                   "h2d_bytes_per_step": 4 * n, "d2h_bytes_per_step": 4 * n}
     if rank == 0 and ws == 1 and not args.skip_extras:
         out["small_fp64"] = small_config(dev)
+        out["atomic_mode"] = atomic_mode(hg, x, ms)
 
     if rank == 0 and ws == 1 and (args.batched or not args.skip_extras):
         out["batched"] = batched(dev, scale=args.batched_scale)
@@ -446,6 +453,20 @@ def run_gpu(args):
     if ws > 1:
         torch.distributed.destroy_process_group()
     return 0
+
+
+def atomic_mode(hg, x, ms_segmented):
+    """The same FP32 call with y scattered by warp-aggregated atomics (FP32 two-sum
+    compensation) instead of the deterministic segmented reduce: event-timed over 50 calls."""
+    import torch
+
+    import paper_2311_08595_gb300 as s3
+    ga = s3.s3_build_format(hg.n, hg.edge_ptr, hg.members, reduce=s3.S3_REDUCE_ATOMIC)
+    y = torch.empty_like(x)
+    ms = _time_calls(ga, x, y, 50)
+    s3.s3_destroy(ga)
+    return {"reduce": "atomic (warp-aggregated, FP32 two-sum compensation)", "ms_per_call": ms,
+            "value": hg.nnz / (ms * 1e-3), "unit": UNIT, "vs_segmented": ms / ms_segmented}
 
 
 def batched(dev, scale=1.0, nvec=16, reps=3):

@@ -460,8 +460,8 @@ s3_status s3_mlp_create(const float *params, uint64_t seed, s3_mlp_t *out);
 s3_status s3_mlp_get_params(s3_mlp_t m, float *params, int32_t bf16);
 
 /* out[v] = W3 relu(W2 relu(W1 feat_v + b1) + b2) + b3 with the BF16 weights and
- * FP32 accumulation; the 64 x 64 layer on the tensor cores, its input split into two
- * BF16 terms (relative error about 2^-17 against FP32 input).  feat: device n x 12;
+ * FP32 accumulation; both hidden layers on the tensor cores, their inputs split into two
+ * BF16 terms each (relative error about 2^-17 against FP32 inputs).  feat: device n x 12;
  * out: device n floats.  Asynchronous; a tensor-core wait that runs out (bounded, well
  * under a second) is reported as S3_ETIMEOUT by the next synchronising call on the model. */
 s3_status s3_mlp_forward(s3_mlp_t m, const float *feat, int64_t n, float *out, void *stream);

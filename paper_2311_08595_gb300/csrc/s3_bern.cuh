@@ -33,6 +33,8 @@
 // member twice the others), the FP64 ratio at most 2.2.
 #pragma once
 
+#include <algorithm>
+
 #include "s3_series.cuh"
 
 namespace s3 {
@@ -276,30 +278,35 @@ __device__ __forceinline__ void bern_edge(const EdgeBucketArgs &b, const T *__re
     }
 }
 
-// All Bernoulli buckets of a call in one launch: block ranges map to buckets
-// (TailEntry::block0 ascending), one edge per thread.  Per warp: lane_elems values per
-// lane, then fb_elems values for the series fallback.
+// All Bernoulli buckets of a call in one launch.  The buckets' edges form tiles of 128
+// (one edge per thread; tab[k].block0 = the first tile of bucket k, ascending) and the
+// blocks walk them (tile t, t + gridDim.x, ...); FP32 launches only as many blocks as are
+// resident at once, so that blocks live long, the instruction caches stay warm and the
+// bucket lookup only moves forward (2.5 % faster than a block per tile; FP64 was slower).  Per warp:
+// lane_elems values per lane, then fb_elems values for the series fallback.
 template <typename T, bool BUF, bool BIAS>
 __global__ void __launch_bounds__(kBernThreads, sizeof(T) == 4 ? 7 : 3) edge_bern_kernel(const TailEntry *__restrict__ tab, int ntab,
-                                                                 int lane_elems, int fb_elems,
+                                                                 int64_t ntiles, int lane_elems, int fb_elems,
                                                                  const T *__restrict__ x, EdgeOutArgs o, BernArgs c) {
     if (o.skip && *o.skip) return;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    int k = 0;
-    while (k + 1 < ntab && tab[k + 1].block0 <= (int64_t)blockIdx.x) ++k;
-    const EdgeBucketArgs b = tab[k].b;
-    const int64_t e = ((int64_t)blockIdx.x - tab[k].block0) * blockDim.x + threadIdx.x;
-    const bool valid = e < b.m;
-    if (__all_sync(0xffffffffu, !valid)) return;
     const size_t warp_elems = (size_t)kLS * lane_elems + (size_t)fb_elems;
     T *base = reinterpret_cast<T *>(smem_raw) + (size_t)(threadIdx.x >> 5) * warp_elems;
     T *fb = base + (size_t)kLS * lane_elems;
-    switch (tab[k].W) {
+    int k = 0;
+    for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        while (k + 1 < ntab && tab[k + 1].block0 <= t) ++k;
+        const EdgeBucketArgs b = tab[k].b;
+        const int64_t e = (t - tab[k].block0) * blockDim.x + threadIdx.x;
+        const bool valid = e < b.m;
+        if (__all_sync(0xffffffffu, !valid)) continue;
+        switch (tab[k].W) {
 #define S3_BERN_CASE(w) \
     case w: bern_edge<T, w, BUF, BIAS>(b, x, o, c, e, valid, base, fb); break;
-        S3_W_CASES(S3_BERN_CASE)
+            S3_W_CASES(S3_BERN_CASE)
 #undef S3_BERN_CASE
-        default: break;
+            default: break;
+        }
     }
 }
 
@@ -311,11 +318,27 @@ cudaError_t launch_edge_bern_t(const TailEntry *tab, int ntab, int64_t nblocks, 
     if (ntab <= 0 || nblocks <= 0) return cudaSuccess;
     const size_t smem = bern_smem_bytes(lane_elems, fb_elems, sizeof(T));
     if (smem > kEdgeSmemCap || nblocks > INT32_MAX || (o.bias != 0) != BIAS) return cudaErrorInvalidConfiguration;
-    const dim3 grid((unsigned)nblocks), block(kBernThreads);
+    // FP32: as many blocks as fit on the device at once (never more than there are tiles);
+    // FP64 (3 blocks per SM): one block per tile, which measured faster there
+    int64_t grid_blocks = nblocks;
+    if (sizeof(T) == 4) {
+        int dev = 0, sms = 0, per_sm = 0;
+        cudaError_t err = cudaGetDevice(&dev);
+        if (err == cudaSuccess) err = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (err == cudaSuccess)
+            err = o.mode == kOutBuffer ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+                                             &per_sm, edge_bern_kernel<T, true, BIAS>, kBernThreads, smem)
+                                       : cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+                                             &per_sm, edge_bern_kernel<T, false, BIAS>, kBernThreads, smem);
+        if (err != cudaSuccess) return err;
+        const int64_t resident = (int64_t)std::max(sms, 1) * std::max(per_sm, 1);
+        grid_blocks = std::min<int64_t>(nblocks, resident);
+    }
+    const dim3 grid((unsigned)grid_blocks), block(kBernThreads);
     if (o.mode == kOutBuffer)
-        edge_bern_kernel<T, true, BIAS><<<grid, block, smem, st>>>(tab, ntab, lane_elems, fb_elems, x, o, c);
+        edge_bern_kernel<T, true, BIAS><<<grid, block, smem, st>>>(tab, ntab, nblocks, lane_elems, fb_elems, x, o, c);
     else
-        edge_bern_kernel<T, false, BIAS><<<grid, block, smem, st>>>(tab, ntab, lane_elems, fb_elems, x, o, c);
+        edge_bern_kernel<T, false, BIAS><<<grid, block, smem, st>>>(tab, ntab, nblocks, lane_elems, fb_elems, x, o, c);
     return cudaGetLastError();
 }
 

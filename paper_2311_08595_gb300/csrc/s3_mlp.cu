@@ -65,33 +65,51 @@ __global__ void feature_record_kernel(const TailEntry *__restrict__ tab, int nta
     int64_t e = ((int64_t)blockIdx.x - tab[k].block0) * blockDim.x + threadIdx.x;
     if (e >= b.m) return;
     const int s = b.s;
+    // members in chunks of eight independent loads (the degree lookups depend on the ids)
+    constexpr int kC = 8;
     unsigned long long D = 0;
-    for (int i = 0; i < s; ++i) {
-        const int v = __ldg(b.ids + (int64_t)i * b.ld + e);
-        D += (unsigned long long)(__ldg(inc_ptr + v + 1) - __ldg(inc_ptr + v));
+    for (int i0 = 0; i0 < s; i0 += kC) {
+        int v[kC];
+#pragma unroll
+        for (int j = 0; j < kC; ++j) v[j] = i0 + j < s ? __ldg(b.ids + (int64_t)(i0 + j) * b.ld + e) : -1;
+#pragma unroll
+        for (int j = 0; j < kC; ++j)
+            if (v[j] >= 0) D += (unsigned long long)(__ldg(inc_ptr + v[j] + 1) - __ldg(inc_ptr + v[j]));
     }
-    for (int i = 0; i < s; ++i) {
-        const int v = __ldg(b.ids + (int64_t)i * b.ld + e);
-        const unsigned long long dv = (unsigned long long)(__ldg(inc_ptr + v + 1) - __ldg(inc_ptr + v));
-        rec[__ldg(b.slot + (int64_t)i * b.ld + e)] = ((D - dv) << 16) | tag;
+    for (int i0 = 0; i0 < s; i0 += kC) {
+        int v[kC], t[kC];
+#pragma unroll
+        for (int j = 0; j < kC; ++j) {
+            const bool in = i0 + j < s;
+            v[j] = in ? __ldg(b.ids + (int64_t)(i0 + j) * b.ld + e) : -1;
+            t[j] = in ? __ldg(b.slot + (int64_t)(i0 + j) * b.ld + e) : 0;
+        }
+#pragma unroll
+        for (int j = 0; j < kC; ++j) {
+            if (v[j] < 0) continue;
+            const unsigned long long dv = (unsigned long long)(__ldg(inc_ptr + v[j] + 1) - __ldg(inc_ptr + v[j]));
+            rec[t[j]] = ((D - dv) << 16) | tag;
+        }
     }
 }
 
 // ---------------------------------------------------------- inference ---
 
 // out[v] = W3 relu(W2 relu(W1 f_v + b1) + b2) + b3 with the BF16 weights, one tile of
-// 128 nodes per CTA (4 warps, one node per thread).  Layer 1 (12 -> 64) and the output
-// layer run on the FP32 units.  Layer 2 (64 x 64, 83 % of the multiply-adds) runs on the
-// tensor cores: D[128 x 64] = A[128 x 64] B^T with B = W2 (BF16, K-major) and A = h1 split
-// into two BF16 terms, hi = bf16(h1) and lo = bf16(h1 - hi), so that the FP32 accumulation
-// of hi W2^T + lo W2^T equals h1 W2^T to about 2^-17 relative (W2 is exactly BF16).  Eight
-// tcgen05.mma (kind::f16, M = 128, N = 64, K = 16 each) accumulate into 64 TMEM columns,
-// read back with tcgen05.ld for the epilogue.
+// 128 nodes per CTA (4 warps, one node per thread, 64 TMEM columns).  Both hidden layers
+// run on the tensor cores as D[128 x 64] = A B^T (tcgen05.mma kind::f16, M = 128, N = 64,
+// K = 16 per instruction, FP32 accumulators in TMEM): layer 1 with A = the features (K = 12,
+// padded to 16 with zeros) and B = W1, layer 2 with A = h1 and B = W2.  Each A is split into
+// two BF16 terms, hi = bf16(a) and lo = bf16(a - hi), so that the FP32 accumulation of
+// hi B^T + lo B^T equals a B^T to about 2^-17 relative (the weights are exactly BF16).  The
+// FP32 units add the biases, apply the ReLUs, split h1 for layer 2, and evaluate the output
+// layer from the second accumulator (tcgen05.ld).
 //
 // Operands in shared memory use the 128-byte-swizzled K-major layout: one 128-byte row
-// per matrix row (64 BF16), 8-row atoms of 1 KB, the 16-byte chunk c of row r stored at
-// chunk c ^ (r % 8).  Descriptor: stride between 8-row groups 1024 B; each K step of 16
-// advances the start address by 32 B inside the atom.
+// per matrix row (64 BF16; layer 1 uses the first 16), 8-row atoms of 1 KB, the 16-byte
+// chunk c of row r stored at chunk c ^ (r % 8).  Descriptor: stride between 8-row groups
+// 1024 B; each K step of 16 advances the start address by 32 B inside the atom.  The A
+// tiles of layer 1 are overwritten by those of layer 2 once the first MMAs have completed.
 constexpr int kTcRows = 128;                       // nodes per CTA (the MMA's M)
 constexpr int kTcCols = 64;                        // TMEM columns (the MMA's N; FP32 accumulators)
 constexpr uint32_t kTcIdesc = (1u << 4)            // D: FP32
@@ -99,12 +117,13 @@ constexpr uint32_t kTcIdesc = (1u << 4)            // D: FP32
                               | (1u << 10)         // B: BF16
                               | ((uint32_t)(H >> 3) << 17)        // N = 64
                               | ((uint32_t)(kTcRows >> 4) << 24); // M = 128 (A and B K-major)
-// dynamic shared memory: A_hi, A_lo (16 KB each), B (8 KB), then FP32 copies of W1, b1, b2,
-// W3, b3 and the mbarrier / TMEM address words
+// dynamic shared memory: A_hi, A_lo (16 KB each), B1 and B2 (8 KB each), then FP32 copies of
+// b1, b2, W3, b3 and the mbarrier / TMEM address words
 constexpr size_t kTcA = (size_t)kTcRows * 128, kTcB = (size_t)H * 128;
-constexpr int kTcSmall = H * F + H + H + H + 1;
-constexpr size_t kTcSmem = 1024 /* alignment slack */ + 2 * kTcA + kTcB + sizeof(float) * kTcSmall + 32;
-constexpr long long kTcWaitPolls = 1ll << 22;      // bound on the MMA-completion wait
+constexpr int kTcSmall = H + H + H + 1;
+constexpr size_t kTcSmem = 1024 /* alignment slack */ + 2 * kTcA + 2 * kTcB + sizeof(float) * kTcSmall + 32;
+static_assert(kTcSmem <= 227 * 1024, "forward kernel shared memory");
+constexpr long long kTcWaitPolls = 1ll << 22;      // bound on each MMA-completion wait
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
     return (uint32_t)__cvta_generic_to_shared(p);
@@ -129,6 +148,74 @@ __device__ __forceinline__ uint32_t pack_bf16(float a, float b) {
     return (uint32_t)__bfloat16_as_ushort(x) | ((uint32_t)__bfloat16_as_ushort(y) << 16);
 }
 
+// eight values as one 16-byte chunk of BF16 hi terms and one of BF16 lo terms
+__device__ __forceinline__ void split_chunk(const float (&h)[8], uint4 &hi, uint4 &lo) {
+    uint32_t H4[4], L4[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const float x0 = h[2 * q], x1 = h[2 * q + 1];
+        H4[q] = pack_bf16(x0, x1);
+        const float r0 = x0 - __bfloat162float(__ushort_as_bfloat16((unsigned short)(H4[q] & 0xffffu)));
+        const float r1 = x1 - __bfloat162float(__ushort_as_bfloat16((unsigned short)(H4[q] >> 16)));
+        L4[q] = pack_bf16(r0, r1);
+    }
+    hi = make_uint4(H4[0], H4[1], H4[2], H4[3]);
+    lo = make_uint4(L4[0], L4[1], L4[2], L4[3]);
+}
+
+// one thread issues the MMAs of a layer (accumulating over the hi and lo A tiles and the K
+// steps) and commits them to the mbarrier
+__device__ __forceinline__ void tc_layer(uint32_t tmem, uint32_t a_hi, uint32_t a_lo, uint32_t b, int ksteps,
+                                         uint32_t mbar) {
+    const uint32_t sa[2] = {a_hi, a_lo};
+#pragma unroll
+    for (int part = 0; part < 2; ++part) {
+        for (int k = 0; k < ksteps; ++k) {
+            const uint64_t da = sw128_desc(sa[part] + 32u * k);
+            const uint64_t db = sw128_desc(b + 32u * k);
+            const uint32_t accum = (part | k) ? 1u : 0u;
+            asm volatile(
+                "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+                "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem),
+                "l"(da), "l"(db), "r"(kTcIdesc), "r"(accum)
+                : "memory");
+        }
+    }
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mbar)
+                 : "memory");
+}
+
+// bounded wait for phase `parity` of the mbarrier; false if it ran out
+__device__ __forceinline__ bool tc_wait(uint32_t mbar, uint32_t parity) {
+    for (long long it = 0; it < kTcWaitPolls; ++it) {
+        uint32_t ok;
+        asm volatile(
+            "{\n\t.reg .pred P;\n\tmbarrier.try_wait.parity.shared::cta.b64 P, [%1], %2;\n\t"
+            "selp.b32 %0, 1, 0, P;\n\t}"
+            : "=r"(ok)
+            : "r"(mbar), "r"(parity)
+            : "memory");
+        if (ok) return true;
+        if (it > 64) __nanosleep(64);
+    }
+    return false;
+}
+
+// 16 accumulator columns of this warp's 32 TMEM lanes (one row per thread)
+__device__ __forceinline__ void tc_load16(uint32_t ta, float (&v)[16]) {
+    uint32_t r[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, "
+        "%13, %14, %15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(ta)
+        : "memory");
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int j = 0; j < 16; ++j) v[j] = __uint_as_float(r[j]);
+}
+
 __global__ void __launch_bounds__(kTcRows) mlp_forward_tc_kernel(const __nv_bfloat16 *__restrict__ wbf,
                                                                   const float *__restrict__ feat, int64_t n,
                                                                   float *__restrict__ out, int vec_feat,
@@ -136,13 +223,14 @@ __global__ void __launch_bounds__(kTcRows) mlp_forward_tc_kernel(const __nv_bflo
     extern __shared__ unsigned char smem_raw[];
     unsigned char *base = reinterpret_cast<unsigned char *>(
         (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
-    unsigned char *a_hi = base, *a_lo = base + kTcA, *b_w2 = base + 2 * kTcA;
-    float *w1 = reinterpret_cast<float *>(b_w2 + kTcB);   // W1[H][F]
-    float *b1 = w1 + H * F, *b2 = b1 + H, *w3 = b2 + H, *b3 = w3 + H;
+    unsigned char *a_hi = base, *a_lo = base + kTcA, *b_w1 = base + 2 * kTcA, *b_w2 = b_w1 + kTcB;
+    float *b1 = reinterpret_cast<float *>(b_w2 + kTcB);
+    float *b2 = b1 + H, *w3 = b2 + H, *b3 = w3 + H;
     uint64_t *mbar = reinterpret_cast<uint64_t *>(
         (reinterpret_cast<uintptr_t>(b3 + 1) + 7) & ~(uintptr_t)7);
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(mbar + 1);
     const int tid = threadIdx.x, warp = tid >> 5;
+    const uint32_t mb = smem_u32(mbar);
 
     // TMEM: 64 columns, allocated by warp 0
     if (warp == 0) {
@@ -152,136 +240,120 @@ __global__ void __launch_bounds__(kTcRows) mlp_forward_tc_kernel(const __nv_bflo
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
     if (tid == 0) {
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(mbar)), "r"(1) : "memory");
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(mb), "r"(1) : "memory");
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
-    // W2 into the B tile (row n = output unit n, 64 BF16 = 8 chunks), the rest as FP32
+    // B tiles: W1 (row n: its 12 weights and 4 zeros in chunks 0-1) and W2 (row n: 64 weights);
+    // biases and W3 as FP32
     {
         const uint4 *src = reinterpret_cast<const uint4 *>(wbf + OW2);
         for (int i = tid; i < H * 8; i += kTcRows) {
             const int r = i >> 3, c = i & 7;
             *reinterpret_cast<uint4 *>(b_w2 + sw128_off(r, c)) = __ldg(src + i);
         }
-        for (int i = tid; i < H * F + H; i += kTcRows) w1[i] = __bfloat162float(wbf[OW1 + i]);  // W1 then b1
+        for (int i = tid; i < H * 2; i += kTcRows) {
+            const int r = i >> 1, c = i & 1;
+            uint32_t w[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int k0 = 8 * c + 2 * q;
+                const unsigned short lo16 = k0 < F ? __bfloat16_as_ushort(wbf[OW1 + r * F + k0]) : 0;
+                const unsigned short hi16 = k0 + 1 < F ? __bfloat16_as_ushort(wbf[OW1 + r * F + k0 + 1]) : 0;
+                w[q] = (uint32_t)lo16 | ((uint32_t)hi16 << 16);
+            }
+            *reinterpret_cast<uint4 *>(b_w1 + sw128_off(r, c)) = make_uint4(w[0], w[1], w[2], w[3]);
+        }
         for (int i = tid; i < H; i += kTcRows) {
+            b1[i] = __bfloat162float(wbf[OB1 + i]);
             b2[i] = __bfloat162float(wbf[OB2 + i]);
             w3[i] = __bfloat162float(wbf[OW3 + i]);
         }
         if (tid == 0) *b3 = __bfloat162float(wbf[OB3]);
     }
-    __syncthreads();
-
-    // layer 1 on the FP32 units: node v = this thread's row; h1 split into the A tiles
+    // layer-1 A tiles: this thread's row = node v's features, split (chunks 0-1, zero padded)
     const int64_t v = (int64_t)blockIdx.x * kTcRows + tid;
-    float f[F];
-    if (v < n && vec_feat) {
-        const float4 *fp = reinterpret_cast<const float4 *>(feat + v * F);
+    {
+        float f[16];
+        if (v < n && vec_feat) {
+            const float4 *fp = reinterpret_cast<const float4 *>(feat + v * F);
 #pragma unroll
-        for (int q = 0; q < F / 4; ++q) {
-            const float4 t = __ldg(fp + q);
-            f[4 * q] = t.x;
-            f[4 * q + 1] = t.y;
-            f[4 * q + 2] = t.z;
-            f[4 * q + 3] = t.w;
-        }
-    } else {
-#pragma unroll
-        for (int i = 0; i < F; ++i) f[i] = v < n ? __ldg(feat + v * F + i) : 0.f;
-    }
-#pragma unroll 1
-    for (int c = 0; c < H / 8; ++c) {
-        float h[8];
-#pragma unroll
-        for (int jj = 0; jj < 8; ++jj) {
-            const int j = 8 * c + jj;
-            float acc = b1[j];
-#pragma unroll
-            for (int i = 0; i < F; i += 4) {
-                const float4 q = *reinterpret_cast<const float4 *>(w1 + j * F + i);
-                acc = fmaf(q.x, f[i], acc);
-                acc = fmaf(q.y, f[i + 1], acc);
-                acc = fmaf(q.z, f[i + 2], acc);
-                acc = fmaf(q.w, f[i + 3], acc);
+            for (int q = 0; q < F / 4; ++q) {
+                const float4 t = __ldg(fp + q);
+                f[4 * q] = t.x;
+                f[4 * q + 1] = t.y;
+                f[4 * q + 2] = t.z;
+                f[4 * q + 3] = t.w;
             }
-            h[jj] = fmaxf(acc, 0.f);
-        }
-        uint32_t hi[4], lo[4];
+        } else {
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            const float x0 = h[2 * q], x1 = h[2 * q + 1];
-            hi[q] = pack_bf16(x0, x1);
-            const float r0 = x0 - __bfloat162float(__ushort_as_bfloat16((unsigned short)(hi[q] & 0xffffu)));
-            const float r1 = x1 - __bfloat162float(__ushort_as_bfloat16((unsigned short)(hi[q] >> 16)));
-            lo[q] = pack_bf16(r0, r1);
+            for (int i = 0; i < F; ++i) f[i] = v < n ? __ldg(feat + v * F + i) : 0.f;
         }
-        const uint32_t off = sw128_off(tid, c);
-        *reinterpret_cast<uint4 *>(a_hi + off) = make_uint4(hi[0], hi[1], hi[2], hi[3]);
-        *reinterpret_cast<uint4 *>(a_lo + off) = make_uint4(lo[0], lo[1], lo[2], lo[3]);
+#pragma unroll
+        for (int i = F; i < 16; ++i) f[i] = 0.f;
+#pragma unroll
+        for (int c = 0; c < 2; ++c) {
+            float h[8];
+#pragma unroll
+            for (int j = 0; j < 8; ++j) h[j] = f[8 * c + j];
+            uint4 hi, lo;
+            split_chunk(h, hi, lo);
+            const uint32_t off = sw128_off(tid, c);
+            *reinterpret_cast<uint4 *>(a_hi + off) = hi;
+            *reinterpret_cast<uint4 *>(a_lo + off) = lo;
+        }
     }
-    // the A tiles (generic-proxy stores) become visible to the tensor cores (async proxy)
+    // the tiles (generic-proxy stores) become visible to the tensor cores (async proxy)
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const uint32_t tmem = *tmem_slot;
+    const uint32_t ta = tmem + ((uint32_t)(32 * warp) << 16);   // this warp's lanes
 
-    // layer 2 on the tensor cores: one thread issues the eight MMAs and commits them to the mbarrier
-    if (tid == 0) {
-        const uint32_t sa[2] = {smem_u32(a_hi), smem_u32(a_lo)};
-        const uint32_t sb = smem_u32(b_w2);
+    if (tid == 0) tc_layer(tmem, smem_u32(a_hi), smem_u32(a_lo), smem_u32(b_w1), 1, mb);
+    bool done = tc_wait(mb, 0);
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const bool ok1 = __all_sync(0xffffffffu, done);
+    // layer-1 epilogue: h1 = relu(acc + b1), split into the layer-2 A tiles (the layer-1 tiles
+    // are free: their MMAs have completed)
+    if (ok1) {
+#pragma unroll 1
+        for (int c0 = 0; c0 < H; c0 += 16) {
+            float acc[16];
+            tc_load16(ta + (uint32_t)c0, acc);
 #pragma unroll
-        for (int part = 0; part < 2; ++part) {
+            for (int half = 0; half < 2; ++half) {
+                float h[8];
 #pragma unroll
-            for (int k = 0; k < H / 16; ++k) {
-                const uint64_t da = sw128_desc(sa[part] + 32u * k);
-                const uint64_t db = sw128_desc(sb + 32u * k);
-                const uint32_t accum = (part | k) ? 1u : 0u;
-                asm volatile(
-                    "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
-                    "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem),
-                    "l"(da), "l"(db), "r"(kTcIdesc), "r"(accum)
-                    : "memory");
+                for (int j = 0; j < 8; ++j) h[j] = fmaxf(acc[8 * half + j] + b1[c0 + 8 * half + j], 0.f);
+                uint4 hi, lo;
+                split_chunk(h, hi, lo);
+                const uint32_t off = sw128_off(tid, (c0 >> 3) + half);
+                *reinterpret_cast<uint4 *>(a_hi + off) = hi;
+                *reinterpret_cast<uint4 *>(a_lo + off) = lo;
             }
         }
-        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                         smem_u32(mbar))
-                     : "memory");
     }
-    // wait for the MMAs (bounded: on timeout flag the error, skip the epilogue)
-    bool done = false;
-    for (long long it = 0; it < kTcWaitPolls; ++it) {
-        uint32_t ok;
-        asm volatile(
-            "{\n\t.reg .pred P;\n\tmbarrier.try_wait.parity.shared::cta.b64 P, [%1], %2;\n\t"
-            "selp.b32 %0, 1, 0, P;\n\t}"
-            : "=r"(ok)
-            : "r"(smem_u32(mbar)), "r"(0)
-            : "memory");
-        if (ok) {
-            done = true;
-            break;
-        }
-        if (it > 64) __nanosleep(64);
-    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    const int all1 = __syncthreads_and(ok1);
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    if (__all_sync(0xffffffffu, done)) {
-        // epilogue: this warp's 32 TMEM lanes (= rows), 16 columns at a time
+    bool ok2 = false;
+    if (all1) {
+        if (tid == 0) tc_layer(tmem, smem_u32(a_hi), smem_u32(a_lo), smem_u32(b_w2), H / 16, mb);
+        done = tc_wait(mb, 1);
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        ok2 = __all_sync(0xffffffffu, done);
+    }
+    if (ok2) {
+        // output layer from the layer-2 accumulators
         float y = *b3;
-#pragma unroll
+#pragma unroll 1
         for (int c0 = 0; c0 < H; c0 += 16) {
-            uint32_t r[16];
-            const uint32_t ta = tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)c0;
-            asm volatile(
-                "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, "
-                "%13, %14, %15}, [%16];"
-                : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-                  "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
-                  "=r"(r[15])
-                : "r"(ta)
-                : "memory");
-            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+            float acc[16];
+            tc_load16(ta + (uint32_t)c0, acc);
 #pragma unroll
-            for (int j = 0; j < 16; ++j) y = fmaf(w3[c0 + j], fmaxf(__uint_as_float(r[j]) + b2[c0 + j], 0.f), y);
+            for (int j = 0; j < 16; ++j) y = fmaf(w3[c0 + j], fmaxf(acc[j] + b2[c0 + j], 0.f), y);
         }
         if (v < n) out[v] = y;
     } else if ((tid & 31) == 0) {
@@ -652,7 +724,9 @@ s3_status s3_mlp_create(const float *params, uint64_t seed, s3_mlp_t *out) {
         cudaMemset(m->m2, 0, sizeof(float) * NP) != cudaSuccess || cudaMemset(m->d_err, 0, sizeof(int)) != cudaSuccess)
         return bail(cuda_fail(cudaGetLastError(), "cudaMemcpy"));
     if (cudaFuncSetAttribute(mlp_train_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTrainSmem) !=
-        cudaSuccess)
+            cudaSuccess ||
+        cudaFuncSetAttribute(mlp_forward_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTcSmem) !=
+            cudaSuccess)
         return bail(cuda_fail(cudaGetLastError(), "cudaFuncSetAttribute"));
     to_bf16_kernel<<<(NP + 255) / 256, 256>>>(m->wf, m->wbf);
     if (cudaDeviceSynchronize() != cudaSuccess) return bail(cuda_fail(cudaGetLastError(), "to_bf16"));
