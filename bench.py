@@ -188,12 +188,18 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def csrc_digest():
-    """sha256 over the library's kernel and host sources (names and contents)."""
+# the sources the FP32 Bernoulli kernel is compiled from (its translation unit and headers)
+BERN_KERNEL_SOURCES = ("s3_bern.cuh", "s3_bern_f32.cu", "s3_series.cuh", "s3_kernels.h")
+
+
+def csrc_digest(names=None):
+    """sha256 over the library's sources (names and contents): all of them, or the given ones."""
     import glob
     import hashlib
     h = hashlib.sha256()
-    for p in sorted(glob.glob(os.path.join(ROOT, "paper_2311_08595_gb300", "csrc", "*"))):
+    csrc = os.path.join(ROOT, "paper_2311_08595_gb300", "csrc")
+    paths = sorted(glob.glob(os.path.join(csrc, "*"))) if names is None else [os.path.join(csrc, n) for n in names]
+    for p in paths:
         h.update(os.path.basename(p).encode())
         with open(p, "rb") as f:
             h.update(f.read())
@@ -359,7 +365,7 @@ def run_gpu(args):
     if os.path.exists(tp):
         try:
             tj = json.load(open(tp))
-            if tj.get("csrc_digest") == csrc_digest():
+            if tj.get("kernel_digest") == csrc_digest(BERN_KERNEL_SOURCES):
                 traffic = tj["bytes_per_member"] * bern_members
                 traffic_note = ("dram__bytes_read.sum + dram__bytes_write.sum of edge_bern_kernel<float> on "
                                 + tj["workload"] + f" ({tj['members']} members), scaled to {bern_members} members")

@@ -65,31 +65,15 @@ __global__ void feature_record_kernel(const TailEntry *__restrict__ tab, int nta
     int64_t e = ((int64_t)blockIdx.x - tab[k].block0) * blockDim.x + threadIdx.x;
     if (e >= b.m) return;
     const int s = b.s;
-    // members in chunks of eight independent loads (the degree lookups depend on the ids)
-    constexpr int kC = 8;
     unsigned long long D = 0;
-    for (int i0 = 0; i0 < s; i0 += kC) {
-        int v[kC];
-#pragma unroll
-        for (int j = 0; j < kC; ++j) v[j] = i0 + j < s ? __ldg(b.ids + (int64_t)(i0 + j) * b.ld + e) : -1;
-#pragma unroll
-        for (int j = 0; j < kC; ++j)
-            if (v[j] >= 0) D += (unsigned long long)(__ldg(inc_ptr + v[j] + 1) - __ldg(inc_ptr + v[j]));
+    for (int i = 0; i < s; ++i) {
+        const int v = __ldg(b.ids + (int64_t)i * b.ld + e);
+        D += (unsigned long long)(__ldg(inc_ptr + v + 1) - __ldg(inc_ptr + v));
     }
-    for (int i0 = 0; i0 < s; i0 += kC) {
-        int v[kC], t[kC];
-#pragma unroll
-        for (int j = 0; j < kC; ++j) {
-            const bool in = i0 + j < s;
-            v[j] = in ? __ldg(b.ids + (int64_t)(i0 + j) * b.ld + e) : -1;
-            t[j] = in ? __ldg(b.slot + (int64_t)(i0 + j) * b.ld + e) : 0;
-        }
-#pragma unroll
-        for (int j = 0; j < kC; ++j) {
-            if (v[j] < 0) continue;
-            const unsigned long long dv = (unsigned long long)(__ldg(inc_ptr + v[j] + 1) - __ldg(inc_ptr + v[j]));
-            rec[t[j]] = ((D - dv) << 16) | tag;
-        }
+    for (int i = 0; i < s; ++i) {
+        const int v = __ldg(b.ids + (int64_t)i * b.ld + e);
+        const unsigned long long dv = (unsigned long long)(__ldg(inc_ptr + v + 1) - __ldg(inc_ptr + v));
+        rec[__ldg(b.slot + (int64_t)i * b.ld + e)] = ((D - dv) << 16) | tag;
     }
 }
 

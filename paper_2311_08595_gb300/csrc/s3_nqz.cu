@@ -20,6 +20,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <climits>
 #include <chrono>
 #include <cmath>
 #include <cstring>
@@ -45,15 +46,6 @@ __device__ __forceinline__ double rcp_seed(double y) {
     return (double)__frcp_rn(my) * Arith<double>::pow2(-ey);
 }
 
-// a / y for y > 0: the FP32-accurate quotient q = a r0 (r0 = rcp_seed(y)) and one correction
-// with the exact residual a - q y (an FMA), which leaves a relative error of about 2^-44 plus
-// the roundings -- the FP64 units' division sequence costs several times more.
-__device__ __forceinline__ double div_refined(double a, double y) {
-    const double r0 = rcp_seed(y);
-    const double q = a * r0;
-    return fma(fma(-q, y, a), r0, q);
-}
-
 // r = a^(1/k) for a > 0: FP32 guess then one Newton step in FP64.
 __device__ __forceinline__ double root_k(double a, int k) {
     if (!(a > 0.0)) return 0.0;
@@ -74,6 +66,103 @@ __device__ __forceinline__ double root_k(double a, int k) {
     // the step's own size is ~1e-7 r, so its divisor needs FP32 accuracy only
     r = r - fma(rk1, r, -b) * rcp_seed((double)k * rk1);
     return r * Arith<double>::pow2(q);
+}
+
+// ---- the per-node pass in double-float arithmetic (pairs of FP32, struct DF) -------------
+// GB300 runs FP32 at 64x its FP64 rate, so the roots and ratios of the per-node pass are
+// computed on the FP32 units with about 46 significant bits; only the iterate's store and
+// its 1-norm stay FP64.
+
+// a positive normal number as a double-float mantissa in [0.5, 1) and its exponent, by
+// integer operations on its bits (the lower 29 bits of a double's significand go to lo)
+__device__ __forceinline__ DF mant_df(double a, int &ea) {
+    const unsigned long long bits = (unsigned long long)__double_as_longlong(a);
+    ea = (int)((bits >> 52) & 0x7ff) - 1022;
+    const unsigned long long M = (bits & 0xFFFFFFFFFFFFFull) | (1ull << 52);
+    const float hi = __uint_as_float((126u << 23) | (unsigned)((M >> 29) & 0x7FFFFFull));
+    const float lo = __fmul_rn(__uint2float_rn((unsigned)(M & 0x1FFFFFFFull)), 0x1p-53f);
+    return DF{hi, lo};
+}
+__device__ __forceinline__ DF mant_df(float a, int &ea) {
+    const unsigned bits = __float_as_uint(a);
+    ea = (int)((bits >> 23) & 0xffu) - 126;
+    return DF{__uint_as_float((126u << 23) | (bits & 0x7FFFFFu)), 0.f};
+}
+__device__ __forceinline__ bool pos_normal(double a) {
+    const unsigned long long bits = (unsigned long long)__double_as_longlong(a);
+    const unsigned ef = (unsigned)((bits >> 52) & 0x7ff);
+    return (bits >> 63) == 0 && ef != 0 && ef != 0x7ff;
+}
+__device__ __forceinline__ bool pos_normal(float a) {
+    const unsigned bits = __float_as_uint(a);
+    const unsigned ef = (bits >> 23) & 0xffu;
+    return (bits >> 31) == 0 && ef != 0 && ef != 0xff;
+}
+
+// 2^p as a float, -126 <= p <= 127
+__device__ __forceinline__ float pow2f(int p) { return __uint_as_float((unsigned)(p + 127) << 23); }
+
+// h^k, k >= 1, by left-to-right binary powering
+__device__ __forceinline__ DF df_pow(DF h, int k) {
+    DF r = h;
+    for (int b = 30 - __clz(k); b >= 0; --b) {
+        r = r * r;
+        if ((k >> b) & 1) r = r * h;
+    }
+    return r;
+}
+
+// a / b for b > 0: the FP32 quotient and one correction from the double-float residual
+__device__ __forceinline__ DF df_div(DF a, DF b) {
+    const float rb = __frcp_rn(b.hi);
+    const float q0 = __fmul_rn(a.hi, rb);
+    const DF p = DF{q0, 0.f} * b;
+    const DF r = a + DF{-p.hi, -p.lo};
+    return df_fast_two_sum(q0, __fmul_rn(__fadd_rn(r.hi, r.lo), rb));
+}
+
+// b^(1/k) for b in [0.5, 2^(k-1)): FP32 seed, then two Newton steps r <- r - (r^k - b) / (k r^(k-1))
+// with the residual in double-float (the divisor needs FP32 accuracy only)
+__device__ __forceinline__ DF root_df(DF b, int k) {
+    if (k == 1) return b;
+    DF r{powf(b.hi, 1.0f / (float)k), 0.f};
+#pragma unroll 1
+    for (int step = 0; step < 2; ++step) {
+        const DF rk1 = df_pow(r, k - 1);
+        const DF res = rk1 * r + DF{-b.hi, -b.lo};
+        // rk1 < 2^(k-1) <= 2^126: its reciprocal is a normal float; 1/k separately (k rk1 may overflow)
+        const float corr = __fmul_rn(__fmul_rn(__fadd_rn(res.hi, res.lo), __frcp_rn(rk1.hi)), __frcp_rn((float)k));
+        r = r + DF{-corr, 0.f};
+    }
+    return r;
+}
+
+// ratio m 2^E with m (double-float) in [0.5, 1): ordered by E, then m
+struct DFE {
+    DF m;
+    int E;
+};
+__device__ __forceinline__ bool dfe_less(const DFE &a, const DFE &b) {
+    return a.E < b.E || (a.E == b.E && (a.m.hi < b.m.hi || (a.m.hi == b.m.hi && a.m.lo < b.m.lo)));
+}
+
+// z / x^k from the biased zt = zm 2^ez and x = m 2^ex (zm, m in [0.5, 1)): zt / m^k =
+// (zm / (2m)^k) 2^(ez + k), with (2m)^k in [1, 2^127) kept in FP32 range
+__device__ __forceinline__ DFE ratio_df(DF zm, int ez, DF m, int k) {
+    const DF pk = df_pow(DF{m.hi * 2.f, m.lo * 2.f}, k);
+    const int pe = (int)((__float_as_uint(pk.hi) >> 23) & 0xffu) - 127;   // pk = pkm 2^pe, pkm in [1, 2)
+    const float sc = pow2f(-pe);
+    DF q = df_div(zm, DF{pk.hi * sc, pk.lo * sc});                          // in (0.25, 1)
+    int E = ez + k - pe;
+    if (q.hi < 0.5f) {
+        q = DF{q.hi * 2.f, q.lo * 2.f};
+        --E;
+    }
+    return DFE{q, E};
+}
+
+__device__ __forceinline__ double dfe_to_double(const DFE &a) {
+    return ((double)a.m.hi + (double)a.m.lo) * Arith<double>::pow2(a.E);
 }
 
 // flags[F_COUNT]: blocks of the current after-kernel that have stored their partials
@@ -130,27 +219,33 @@ __global__ void __launch_bounds__(kNqzThreads) nqz_after_kernel(const T *__restr
     __shared__ double sa[kNqzThreads / 32], sb[kNqzThreads / 32];
     __shared__ int last;
     double acc = 0.0, lo = INFINITY, hi = -INFINITY;
+    DFE rlo{DF{1.f, 0.f}, INT_MAX}, rhi{DF{0.5f, 0.f}, INT_MIN};
     bool bad = false;
     for (int64_t v = (int64_t)blockIdx.x * kNqzThreads + threadIdx.x; v < n; v += (int64_t)gridDim.x * kNqzThreads) {
-        const double z = (double)zt[v];
-        const double xv = (double)xin[v];
-        const int e = Arith<double>::expo(xv);
-        const double r = root_k(z, k) * Arith<double>::pow2(e);
-        bad |= !(z > 0.0) || !isfinite(z);
-        u[v] = r;
-        acc += r;
-        if (!first) {
-            const double m = xv * Arith<double>::pow2(-e);
-            double pk = 1.0, base = m;
-            for (int q = k; q > 0; q >>= 1) {
-                if (q & 1) pk *= base;
-                base *= base;
-            }
-            const double ratio = div_refined(z, pk);
-            bad |= !isfinite(ratio) || !(ratio > 0.0);
-            lo = fmin(lo, ratio);
-            hi = fmax(hi, ratio);
+        const T zv = zt[v], xv = xin[v];
+        if (!pos_normal(zv) || !pos_normal(xv)) {
+            bad = true;
+            u[v] = 0.0;
+            continue;
         }
+        int ez, ex;
+        const DF zm = mant_df(zv, ez), m = mant_df(xv, ex);
+        // zt = b 2^(q k) with b = zm 2^rem in [0.5, 2^(k-1)); z^(1/k) = b^(1/k) 2^(q + ex)
+        const int q = ez >= 0 ? ez / k : -((-ez + k - 1) / k);
+        const float sb = pow2f(ez - q * k);
+        const DF r = root_df(DF{zm.hi * sb, zm.lo * sb}, k);
+        const double rv = ((double)r.hi + (double)r.lo) * Arith<double>::pow2(q + ex);
+        u[v] = rv;
+        acc += rv;
+        if (!first) {
+            const DFE ratio = ratio_df(zm, ez, m, k);
+            if (dfe_less(ratio, rlo)) rlo = ratio;
+            if (dfe_less(rhi, ratio)) rhi = ratio;
+        }
+    }
+    if (!first && rlo.E != INT_MAX) {
+        lo = dfe_to_double(rlo);
+        hi = dfe_to_double(rhi);
     }
     const int any_bad = __syncthreads_or(bad);
     const double bsum = block_sum(acc, sa);
