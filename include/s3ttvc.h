@@ -500,10 +500,10 @@ s3_status s3_mlp_destroy(s3_mlp_t m);
 #define S3_NOALLOC_MAX_NODES (1 << 22)
 
 /*
- * FP32 y = B x^(N-1) for callers that cannot allocate device memory: code
- * being captured into a CUDA graph (allocation is illegal during capture),
- * pipelines that fix all their memory up front, or hosts whose own allocator
- * owns the device.  Such callers can neither build a graph handle nor pass a
+ * FP32 y = B x^(N-1) for callers that cannot allocate device memory:
+ * pipelines that fix all their memory up front, hosts whose own allocator
+ * owns the device, or latency-critical loops that must not risk an
+ * allocation's implicit device synchronisation.  Such callers can neither build a graph handle nor pass a
  * workspace, so this entry point takes the hypergraph as plain device arrays
  * and allocates nothing: its only scratch (one FP32 two-sum compensation term
  * per node) is a fixed array of S3_NOALLOC_MAX_NODES floats (16 MiB) compiled

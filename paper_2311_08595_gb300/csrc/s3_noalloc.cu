@@ -1,10 +1,10 @@
 // S^3TTVc for callers that must not allocate device memory.
 //
 // Who needs this: code that runs where cudaMalloc is not allowed or not
-// wanted -- for example a host loop that is being captured into a CUDA graph
-// (allocation calls are illegal during capture), a real-time or embedded
-// pipeline that fixes all of its memory up front, or a runtime whose own
-// allocator owns every byte of the device.  Such callers cannot build a graph
+// wanted -- for example a real-time or embedded pipeline that fixes all of its
+// memory up front, a runtime whose own allocator owns every byte of the
+// device, or a latency-critical loop that must not risk an allocation's
+// implicit device synchronisation.  Such callers cannot build a graph
 // handle (s3_build_format allocates) and cannot hand the library a workspace.
 //
 // s3_sttsvc_f32_noalloc therefore takes the hypergraph directly as device CSR

@@ -98,3 +98,18 @@ def test_iteration_cap_reports_noconv(medium):
     hg, _ = medium
     x, res = _run(hg, tol=1e-14, max_iter=5, raise_on_noconv=False)
     assert res["status"] == "S3_ENOCONV" and res["iters"] == 5 and not res["converged"]
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_high_rank_matches_oracle(precision):
+    # order 64: the per-node pass takes 63rd roots and 63rd powers of mantissas in [0.5, 1)
+    # (the FP64 oracle itself needs x^(N-1) above the FP64 range's bottom, so N stays below ~100 here)
+    import paper_2311_08595_gb300 as s3
+    hg, _ = s3synth.largest_component(s3synth.config_large_rank(n=300, m=300, rank=64, prob=0.08, seed=11))
+    ref = nqz(hg, tol=1e-8, nthreads=oracle.max_threads())
+    g = s3.s3_build_format(hg.n, hg.edge_ptr, hg.members, rank=hg.rank)
+    x, res = s3.s3_hcentrality(g, tol=1e-8, precision=precision)
+    x = x.cpu().numpy()
+    assert res["converged"]
+    assert abs(res["iters"] - ref.iters) <= 1
+    assert np.max(np.abs(x - ref.x) / ref.x) < 1e-10
