@@ -152,13 +152,13 @@ def s3_sttsvc_layout(g, layout, x, y, stream=None, df=False):
     return y
 
 
-def s3_sttsvc_host(g, x_host, y_host, stream=None):
+def s3_sttsvc_host(g, x_host, y_host, stream=None, df=False):
     """Host buffers in and out (torch CPU tensors, pinned recommended, or numpy)."""
     if isinstance(x_host, np.ndarray):
-        code = S3_F32 if x_host.dtype == np.float32 else S3_F64
+        code = S3_F32 if x_host.dtype == np.float32 else (S3_DF64 if df else S3_F64)
         xp, yp = x_host.ctypes.data, y_host.ctypes.data
     else:
-        code = _dtype_code(x_host)
+        code = _dtype_code(x_host, df)
         xp, yp = x_host.data_ptr(), y_host.data_ptr()
     check(load().s3_sttsvc_host(g.handle, code, xp, yp, _stream(stream)))
     return y_host

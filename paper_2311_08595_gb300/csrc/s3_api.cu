@@ -81,6 +81,12 @@ void free_all(s3_graph_s *g) {
     g->ev_done = nullptr;
     if (g->qstream) cudaStreamDestroy(g->qstream);
     g->qstream = nullptr;
+    for (auto &ex : g->host_exec) {
+        if (ex) cudaGraphExecDestroy(ex);
+        ex = nullptr;
+    }
+    if (g->cap_stream) cudaStreamDestroy(g->cap_stream);
+    g->cap_stream = nullptr;
     if (g->h_range) cudaFreeHost(g->h_range);
     g->h_range = nullptr;
 }
@@ -720,10 +726,15 @@ s3_status sttsvc_dispatch(s3_graph_s *g, s3_dtype dt, int32_t layout, const void
 // The call between two stream-ordered reads of the range counter; synchronises st and
 // returns S3_ERANGE when the counter moved (y is written either way).
 s3_status sttsvc_checked(s3_graph_s *g, s3_dtype dt, int32_t layout, const void *x, void *y, cudaStream_t st,
-                         void *y_host, size_t y_bytes) {
+                         void *y_host, size_t y_bytes, cudaGraphExec_t exec = nullptr) {
     S3_CUDA(cudaMemcpyAsync(&g->h_range[0], g->d_range, sizeof(unsigned long long), cudaMemcpyDeviceToHost, st));
-    s3_status s = sttsvc_dispatch(g, dt, layout, x, y, st);
-    if (s != S3_OK) return s;
+    if (exec) {
+        S3_CUDA(cudaGraphLaunch(exec, st));
+    } else {
+        s3_status s = sttsvc_dispatch(g, dt, layout, x, y, st);
+        if (s != S3_OK) return s;
+    }
+    s3_status s;
     if (y_host) S3_CUDA(cudaMemcpyAsync(y_host, y, y_bytes, cudaMemcpyDeviceToHost, st));
     S3_CUDA(cudaMemcpyAsync(&g->h_range[1], g->d_range, sizeof(unsigned long long), cudaMemcpyDeviceToHost, st));
     s = mark_done(g, st);
@@ -775,7 +786,29 @@ s3_status s3_sttsvc_host(s3_graph_t g, s3_dtype dt, const void *x_host, void *y_
     cudaStream_t st = (cudaStream_t)stream;
     const size_t bytes = (dt == S3_F32 ? 4 : 8) * (size_t)g->n;
     S3_CUDA(cudaMemcpyAsync(g->d_xh, x_host, bytes, cudaMemcpyHostToDevice, st));
-    return sttsvc_checked(g, dt, g->opt.layout, g->d_xh, g->d_yh, st, y_host, bytes);
+    // the call on the staging buffers is the same every time: launch it as one captured graph
+    // (captured on the handle's own stream at the first call of each type), which keeps the
+    // dozen launches of a call off the host's critical path between the two copies
+    cudaGraphExec_t &ex = g->host_exec[dt];
+    if (!ex) {
+        if (!g->cap_stream) S3_CUDA(cudaStreamCreateWithFlags(&g->cap_stream, cudaStreamNonBlocking));
+        cudaGraph_t graph = nullptr;
+        S3_CUDA(cudaStreamBeginCapture(g->cap_stream, cudaStreamCaptureModeThreadLocal));
+        s3_status s = sttsvc_dispatch(g, dt, g->opt.layout, g->d_xh, g->d_yh, g->cap_stream);
+        cudaError_t ce = cudaStreamEndCapture(g->cap_stream, &graph);
+        if (s != S3_OK) {
+            if (graph) cudaGraphDestroy(graph);
+            return s;
+        }
+        S3_CUDA(ce);
+        ce = cudaGraphInstantiate(&ex, graph, 0);
+        cudaGraphDestroy(graph);
+        if (ce != cudaSuccess) {
+            ex = nullptr;
+            return cuda_fail(ce, "graph instantiation");
+        }
+    }
+    return sttsvc_checked(g, dt, g->opt.layout, g->d_xh, g->d_yh, st, y_host, bytes, ex);
 }
 
 s3_status s3_sttsvc_profile(s3_graph_t g, s3_dtype dt, const void *x, void *y, s3_profile *prof, void *stream) {

@@ -85,6 +85,10 @@ struct s3_graph_s {
     // range-checked call reads the range counter into (before, after)
     cudaEvent_t ev_done = nullptr;
     cudaStream_t qstream = nullptr;
+    // the host-buffer entry point's call, captured once per series type (x and y are the
+    // handle's staging buffers, so the graph never changes); the stream it was captured on
+    cudaGraphExec_t host_exec[3] = {nullptr, nullptr, nullptr};
+    cudaStream_t cap_stream = nullptr;
     unsigned long long *h_range = nullptr;
     uint32_t *d_feat_scratch = nullptr;  // warm-start feature partials (64 bytes per hub piece)
     s3::TailEntry *d_feat_tab = nullptr; // buckets of the fused feature launch (size bin in W)

@@ -178,15 +178,18 @@ def test_host_entry_point_matches_device():
     import paper_2311_08595_gb300 as s3
     hg = s3synth.config_small(seed=2)
     g = s3.s3_build_format(hg.n, hg.edge_ptr, hg.members)
-    x = s3synth.x_uniform(hg.n, 0, 1, 2)
-    for dt in (torch.float32, torch.float64):
-        xh = torch.tensor(x, dtype=dt).pin_memory()
-        yh = torch.empty_like(xh).pin_memory()
-        s3.s3_sttsvc_host(g, xh, yh)
-        yd = torch.empty(hg.n, dtype=dt, device="cuda")
-        s3.s3_sttsvc(g, xh.cuda(), yd)
-        torch.cuda.synchronize()
-        assert torch.equal(yh, yd.cpu())
+    # each type's first host call captures the call on the handle's staging buffers as a
+    # graph; the later calls replay it with new inputs
+    for dt, df in ((torch.float32, False), (torch.float64, False), (torch.float64, True)):
+        for seed in (2, 3, 4):
+            x = s3synth.x_uniform(hg.n, 0, 1, seed)
+            xh = torch.tensor(x, dtype=dt).pin_memory()
+            yh = torch.empty_like(xh).pin_memory()
+            s3.s3_sttsvc_host(g, xh, yh, df=df)
+            yd = torch.empty(hg.n, dtype=dt, device="cuda")
+            s3.s3_sttsvc(g, xh.cuda(), yd, df=df)
+            torch.cuda.synchronize()
+            assert torch.equal(yh, yd.cpu()), (dt, df, seed)
 
 
 def test_range_events_counted():
