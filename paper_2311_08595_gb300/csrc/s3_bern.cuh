@@ -74,6 +74,18 @@ __device__ __forceinline__ T bern_majorant(const T (&Ha)[W], T xi) {
     return a;
 }
 
+// prod / x for the scaled member values (x near 1, x > 0): FP32 multiplies by the hardware
+// reciprocal (within 2 units in the last place; the division's IEEE sequence and its slow-path
+// branch would sit in the per-member loop); FP64 refines an FP32 reciprocal seed by two Newton
+// steps (relative error below 2^-52 before the product) instead of the FP64 division sequence.
+__device__ __forceinline__ float others_product(float prod, float x) { return __fdividef(prod, x); }
+__device__ __forceinline__ double others_product(double prod, double x) {
+    double r = (double)__frcp_rn((float)x);
+    r = fma(r, fma(-x, r, 1.0), r);
+    r = fma(r, fma(-x, r, 1.0), r);
+    return prod * r;
+}
+
 template <typename T> __device__ __forceinline__ T bern_beta(const BernArgs &c, int k);
 template <> __device__ __forceinline__ float bern_beta<float>(const BernArgs &c, int k) { return c.beta32[k]; }
 template <> __device__ __forceinline__ double bern_beta<double>(const BernArgs &c, int k) { return c.beta64[k]; }
@@ -165,9 +177,9 @@ __device__ __forceinline__ void bern_edge(const EdgeBucketArgs &b, const T *__re
                 if constexpr (BIAS) {
                     // the biased output of the centrality iteration: the scale of each result
                     // depends on its member's exponent, which is at hand here
-                    xs[i * kLS] = scale_result<T>(v * (prod / xi), b, p, Arith<T>::expo(xi) - p, nullptr);
+                    xs[i * kLS] = scale_result<T>(v * others_product(prod, xi), b, p, Arith<T>::expo(xi) - p, nullptr);
                 } else {
-                    xs[i * kLS] = v * (prod / xi);
+                    xs[i * kLS] = v * others_product(prod, xi);
                 }
             }
         } else {
@@ -226,9 +238,9 @@ __device__ __forceinline__ void bern_edge(const EdgeBucketArgs &b, const T *__re
                 if constexpr (BIAS) {
                     // the biased output of the centrality iteration: the scale of each result
                     // depends on its member's exponent, which is at hand here
-                    xs[i * kLS] = scale_result<T>(v * (prod / xi), b, p, Arith<T>::expo(xi) - p, nullptr);
+                    xs[i * kLS] = scale_result<T>(v * others_product(prod, xi), b, p, Arith<T>::expo(xi) - p, nullptr);
                 } else {
-                    xs[i * kLS] = v * (prod / xi);
+                    xs[i * kLS] = v * others_product(prod, xi);
                 }
             }
         }
