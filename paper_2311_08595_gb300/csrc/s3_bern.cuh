@@ -24,7 +24,7 @@
 // recurrence) can cancel.  FP32: with P the positive terms of the sum and Q the
 // magnitude of the negative ones (G's coefficients are sums of positive terms, so
 // P + Q bounds the error mass), an edge is accepted when every member has
-// P + Q <= 4 (P - Q).  FP64: the recurrence runs a second time with |beta_k| (all
+// P + Q <= 4 (P - Q).  FP64: the recurrence runs a second time with |beta_k| (in FP32: all
 // terms >= 0; its result A bounds the rounding error of G coefficient by
 // coefficient) and an edge is accepted when every member has
 // sum_k A[W-1-k] |beta_k| x_i^k <= 64 (P - Q).  Edges that fail, or hold an x <= 0,
@@ -203,29 +203,37 @@ __device__ __forceinline__ void bern_edge(const EdgeBucketArgs &b, const T *__re
             }
             // G = exp(sum_k l_k p_k t^k) with k l_k = beta_k: G_0 = 1,
             // G_m = (1/m) sum_{k=1}^{m} beta_k p_k G_{m-k}; A the same recurrence with |beta_k|
-            // (all terms >= 0), which bounds the rounding error of G
+            // (all terms >= 0), which bounds the rounding error of G.  A only has to bound, not to
+            // be exact: it runs in FP32 (all its terms are positive, so its own relative error
+            // stays below ~2^-18, which the gate's 1e-4 allowance covers), off the FP64 pipe.
     #pragma unroll
             for (int k = 1; k < W; ++k) q[k] *= bern_beta<T>(c, k);
-            T G[W], A[W];
+            float qa[W];
+    #pragma unroll
+            for (int k = 1; k < W; ++k) qa[k] = fabsf((float)q[k]);
+            T G[W];
+            float A[W];
             G[0] = T(1);
-            A[0] = T(1);
+            A[0] = 1.f;
     #pragma unroll
             for (int m = 1; m < W; ++m) {
                 // from k = m down, so that G[m-1] (the value just formed) enters last
-                T acc = T(0), acca = T(0);
+                T acc = T(0);
+                float acca = 0.f;
     #pragma unroll
                 for (int k = m; k >= 1; --k) {
                     acc = Arith<T>::fma_(q[k], G[m - k], acc);
-                    acca = Arith<T>::fma_(Arith<T>::absv(q[k]), A[m - k], acca);
+                    acca = fmaf(qa[k], A[m - k], acca);
                 }
                 G[m] = acc * Num<T>::recip(m);
-                A[m] = acca * Num<T>::recip(m);
+                A[m] = acca * (1.0f / (float)m);
             }
-            T H[W], Ha[W];
+            T H[W];
+            float Ha[W];
     #pragma unroll
             for (int k = 0; k < W; ++k) {
                 H[k] = G[W - 1 - k] * bern_beta<T>(c, k);
-                Ha[k] = A[W - 1 - k] * Arith<T>::absv(bern_beta<T>(c, k));
+                Ha[k] = A[W - 1 - k] * fabsf(c.beta32[k]);
             }
             const T kmax = bern_kmax<T>(c);
             // every member: the Bernoulli sum, its majorant (gate), times prod_{j != i} x_j = P / x_i
@@ -234,7 +242,7 @@ __device__ __forceinline__ void bern_edge(const EdgeBucketArgs &b, const T *__re
                 T Pp, Q;
                 bern_eval<T, W>(H, xi, Pp, Q);
                 const T v = Pp - Q;
-                ok &= bern_majorant<T, W>(Ha, xi) <= kmax * v;
+                ok &= (T)bern_majorant<float, W>(Ha, (float)xi) * T(1.0001) <= kmax * v;
                 if constexpr (BIAS) {
                     // the biased output of the centrality iteration: the scale of each result
                     // depends on its member's exponent, which is at hand here
