@@ -121,13 +121,15 @@ __device__ __forceinline__ DF df_div(DF a, DF b) {
     return df_fast_two_sum(q0, __fmul_rn(__fadd_rn(r.hi, r.lo), rb));
 }
 
-// b^(1/k) for b in [0.5, 2^(k-1)): FP32 seed, then two Newton steps r <- r - (r^k - b) / (k r^(k-1))
-// with the residual in double-float (the divisor needs FP32 accuracy only)
+// b^(1/k) for b in [0.5, 2^(k-1)): FP32 seed (relative error e of a few 2^-24), then one Newton
+// step r <- r - (r^k - b) / (k r^(k-1)) with the residual in double-float (the divisor needs FP32
+// accuracy only): relative error about (k-1) e^2 / 2, about 7e-13 at rank 25 and 4e-12 at rank
+// 128 -- inside what the iteration's 1e-8 bracket and its FP64 results need (a second step, a
+// third of the per-node pass's dependent chain, would not change the iterate that matters)
 __device__ __forceinline__ DF root_df(DF b, int k) {
     if (k == 1) return b;
     DF r{powf(b.hi, 1.0f / (float)k), 0.f};
-#pragma unroll 1
-    for (int step = 0; step < 2; ++step) {
+    {
         const DF rk1 = df_pow(r, k - 1);
         const DF res = rk1 * r + DF{-b.hi, -b.lo};
         // rk1 < 2^(k-1) <= 2^126: its reciprocal is a normal float; 1/k separately (k rk1 may overflow)
