@@ -299,8 +299,9 @@ s3_status s3_nqz_options_init(s3_nqz_options *opt);
  * x_out: device, n doubles, written with the last iterate (1-norm 1).
  * res: host.  Every node must belong to at least one edge (S3_EINVAL
  * otherwise: the ratio z/x^(N-1) is undefined there), and rank >= 2.
- * FP64 is used for the (N-1)-th roots, the 1-norm, the min/max ratios and the
- * test.  Synchronous on ``stream``; returns S3_ENOCONV (x_out and res still
+ * The (N-1)-th roots and the ratios are FP64-accurate (double-float arithmetic on
+ * the FP32 units, relative error below 1e-11 at any rank), the 1-norm, the min/max
+ * and the test FP64.  Synchronous on ``stream``; returns S3_ENOCONV (x_out and res still
  * written) if max_iter passes do not reach tol.
  */
 s3_status s3_hcentrality(s3_graph_t g, const s3_nqz_options *opt, const double *x0, double *x_out,

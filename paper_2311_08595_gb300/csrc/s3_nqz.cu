@@ -9,8 +9,8 @@
 // zt_v = z_v 2^(-(N-1) e_v), where x_v = m_v 2^(e_v), m_v in [0.5, 1), is the
 // vector the call used.  Then z_v^(1/(N-1)) = zt_v^(1/(N-1)) 2^(e_v) and
 // z_v / x_v^(N-1) = zt_v / m_v^(N-1), so neither tiny x (x_v ~ 1/n) nor large
-// ranks push anything out of range.  Roots, the 1-norm, the ratios and their
-// min/max are FP64; the series products are FP64, or FP32 until the gap stops
+// ranks push anything out of range.  Roots and ratios are FP64-accurate (double-float
+// on the FP32 units), the 1-norm and the bracket FP64; the series products are FP64, or FP32 until the gap stops
 // shrinking or drops below switch_tol and then FP64 or double-float (pairs of
 // FP32, S3_DF64), or double-float throughout (the precision option).
 // Iterations run in captured CUDA graphs of `check_every` steps; a device flag
