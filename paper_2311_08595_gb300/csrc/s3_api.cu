@@ -133,9 +133,14 @@ int closed_form_mask(const s3_graph_s *g, size_t k) {
     const double kappa = sgn > 0.0 ? pos / sgn : 1e300;
     const double gate32 = ((double)n + half + 4.0) / 128.0;            // C 2^-24 / 2^-17
     const double gate64 = ((double)s * n + half + 4.0) / 2048.0;       // C 2^-53 / 2^-42
+    // FP64 from size 6 on: the Bernoulli form's power sums cost fewer FP64 operations (its error
+    // majorant runs on the FP32 units): per member 2W, the recurrence W(W-1)/2, per member its
+    // sum, quotient and gate (~W/2 + 14), plus O(W)
+    const double bern64 = s >= 6 ? s * (2.0 * W - 1.0) + 3.0 * (W - 1) + W * (W - 1) / 2.0 + W + s * (W / 2.0 + 14.0)
+                                 : 1e300;
     int mask = 0;
     if (closed32 < 0.8 * series && gate32 * kappa <= 0.5) mask |= 1;
-    if (closed64 < 0.8 * series && gate64 * kappa <= 0.5) mask |= 2;
+    if (closed64 < 0.8 * series && closed64 < bern64 && gate64 * kappa <= 0.5) mask |= 2;
     return mask;
 }
 

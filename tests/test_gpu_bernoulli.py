@@ -53,8 +53,8 @@ def test_bernoulli_matches_oracle(powerlaw):
         for red in (0, 1):
             (y,), q = run(hg, x, dt, reduce=red)
             sizes = q["f32"] if dt == "f32" else q["f64"]
-            # FP32: sizes 6..25 (3..5 closed form); FP64: 7..25 (2..6 closed form)
-            assert sizes == list(range(6 if dt == "f32" else 7, 26)), sizes
+            # FP32 and FP64: sizes 6..25 (the closed form takes 3..5 in FP32, 2..5 in FP64)
+            assert sizes == list(range(6, 26)), sizes
             assert q["rejected"] == 0, q
             e = rel_err(y, want)
             assert e <= tol, f"{dt} reduce={red}: {e:.3e}"
