@@ -492,13 +492,20 @@ __global__ void warm_exp_kernel(const float *__restrict__ out, int64_t n, double
     }
 }
 
+// (blockDim.x = 256) every block sums the partials with all its threads in one fixed order
+// (strided per thread, then a tree), so all blocks scale by the same 1/sum
 __global__ void warm_scale_kernel(double *__restrict__ x0, int64_t n, const double *__restrict__ partial, int np) {
+    __shared__ double sh[256];
     __shared__ double inv;
-    if (threadIdx.x == 0) {
-        double t = 0.0;
-        for (int i = 0; i < np; ++i) t += partial[i];
-        inv = 1.0 / t;
+    double t = 0.0;
+    for (int i = threadIdx.x; i < np; i += blockDim.x) t += partial[i];
+    sh[threadIdx.x] = t;
+    __syncthreads();
+    for (int d = 128; d > 0; d >>= 1) {
+        if ((int)threadIdx.x < d) sh[threadIdx.x] += sh[threadIdx.x + d];
+        __syncthreads();
     }
+    if (threadIdx.x == 0) inv = 1.0 / sh[0];
     __syncthreads();
     for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x)
         x0[v] *= inv;
