@@ -18,9 +18,11 @@ These tests
     the members' series in Horner form, the x^4-Horner split of the sum into its
     positive part P and negative part Q, P / x_i) and check that every member the
     gate (P + Q <= 4 (P - Q)) accepts is within the FP32 tolerance of the exact
-    value, and that the gate rejects badly conditioned edges.  (The FP64 kernel
-    forms G by the power-sum recurrence, checked exactly here and against the
-    oracle at 1e-12 on the GPU.)
+    value, and that the gate rejects badly conditioned edges,
+  * replay the FP64 kernel's order (power sums by a binary tree of products, the
+    recurrence for G in float64, its error majorant in float32, the gate
+    maj <= 64 (P - Q)) and check that accepted members are within 1e-12 of the
+    exact value and that a badly conditioned edge is rejected.
 The GPU tests check the kernels themselves against the oracle.
 """
 from fractions import Fraction
@@ -182,3 +184,106 @@ def test_gate_rejects_badly_conditioned_edges():
     a = [F(0.02)] * 5 + [F(0.8)]
     vals, P, Q = bern_fp32(a, 20)
     assert any(float(P[i] + Q[i]) > 4.0 * float(P[i] - Q[i]) for i in range(6))
+
+
+def bern_exact_all(xs, N):
+    """Every member's exact value of the Bernoulli form (G formed once)."""
+    s = len(xs)
+    W = N - s + 1
+    beta = beta_exact(max(W - 1, 1))
+    G = [Fraction(1)] + [Fraction(0)] * (W - 1)
+    for xj in xs:
+        g = [Fraction(xj) ** k / factorial(k + 1) for k in range(W)]
+        G = [sum(G[m - k] * g[k] for k in range(m + 1)) for m in range(W)]
+    total = Fraction(1)
+    for xj in xs:
+        total *= Fraction(xj)
+    return [total / Fraction(xs[i]) * sum(G[W - 1 - k] * beta[k] * Fraction(xs[i]) ** k for k in range(W))
+            for i in range(s)]
+
+
+def bern_fp64(a, W):
+    """(values, accepted) per member in the FP64 kernel's order: power sums and the recurrence
+    for G in float64, the error majorant A in float32, the gate maj * 1.0001 <= 64 (P - Q)."""
+    D, S = np.float64, np.float32
+    beta = [D(float(b)) for b in beta_exact(max(W - 1, 1))]
+    q = [D(0)] * W
+    prod = D(1)
+    for xi in a:
+        prod = D(prod * xi)
+        pw = [D(1), D(xi)] + [D(0)] * max(W - 2, 0)
+        for k in range(2, W):
+            pw[k] = D(pw[k // 2] * pw[k - k // 2])
+        for k in range(1, W):
+            q[k] = D(q[k] + pw[k])
+    for k in range(1, W):
+        q[k] = D(q[k] * beta[k])
+    qa = [S(abs(v)) for v in q]
+    G, A = [D(1)] + [D(0)] * (W - 1), [S(1)] + [S(0)] * (W - 1)
+    for m in range(1, W):
+        acc, acca = D(0), S(0)
+        for k in range(m, 0, -1):
+            acc = D(q[k] * G[m - k] + acc)
+            acca = S(np.float64(qa[k]) * np.float64(A[m - k]) + np.float64(acca))
+        G[m] = D(acc * D(1.0 / m))
+        A[m] = S(acca * S(1.0 / m))
+    H = [D(G[W - 1 - k] * beta[k]) for k in range(W)]
+    Ha = [S(A[W - 1 - k] * S(abs(float(beta[k])))) for k in range(W)]
+    vals, ok = [], []
+    for xi in a:
+        x2 = D(xi * xi)
+        x4 = D(x2 * x2)
+        p2 = D(0)
+        if W > 2:
+            for k in range(2 + 4 * ((W - 3) // 4), 1, -4):
+                p2 = D(p2 * x4 + H[k])
+        p = H[0]
+        if W > 1:
+            p = D(H[1] * xi + p)
+        P = D(p2 * x2 + p)
+        qn = D(0)
+        if W > 4:
+            for k in range(4 + 4 * ((W - 5) // 4), 3, -4):
+                qn = D(qn * x4 - H[k])
+            qn = D(qn * x4)
+        v = D(P - qn)
+        xf = S(xi)
+        xf2 = S(xf * xf)
+        maj = S(0)
+        for k in range(2 * ((W - 1) // 2), -1, -2):
+            maj = S(maj * xf2 + Ha[k])
+        if W > 1:
+            maj = S(Ha[1] * xf + maj)
+        ok.append(float(maj) * 1.0001 <= 64.0 * float(v))
+        vals.append(D(v * D(prod / xi)))
+    return vals, ok
+
+
+@pytest.mark.parametrize("N", [12, 25])
+def test_fp64_replay_within_tolerance_when_the_gate_accepts(N):
+    # the FP64 kernel's power-sum recurrence with its FP32 majorant: every member the gate
+    # accepts is within the FP64 tolerance of the exact value
+    rng = np.random.default_rng(11 + N)
+    accepted = rejected = 0
+    for s in range(6, N + 1):
+        W = N - s + 1
+        for spread in (1.2, 2.0, 4.0, 16.0, 64.0):
+            a = [np.float64(v) for v in rng.uniform(1.0, spread, size=s) / s]
+            vals, ok = bern_fp64(a, W)
+            if not all(ok):
+                rejected += 1
+                continue
+            accepted += 1
+            want = bern_exact_all([Fraction(float(v)) for v in a], N)
+            for i in range(s):
+                err = abs(Fraction(float(vals[i])) - want[i]) / want[i]
+                assert err <= Fraction(1, 10 ** 12), (N, s, spread, i, float(err))
+    assert accepted > 0
+
+
+def test_fp64_gate_rejects_badly_conditioned_edges():
+    # one member 200 times the others at s = 6, N = 25: the recurrence cancels beyond what the
+    # majorant allows
+    a = [np.float64(0.004)] * 5 + [np.float64(0.8)]
+    _, ok = bern_fp64(a, 20)
+    assert not all(ok)
