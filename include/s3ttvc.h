@@ -116,7 +116,8 @@ typedef struct {
     int32_t closed_form_max_s; /* FP32/FP64 buckets of edges of size 2..this (at most 6) that run
                               their own launch are evaluated in closed form -- the inclusion-exclusion
                               expansion of E(x_v) prod_{u != v} Ebar(x_u) (Sec. II-A) -- where that
-                              costs fewer operations than the series products; every edge whose
+                              costs fewer operations than the series products (and, for FP64 from
+                              size 6 on, fewer FP64 operations than the Bernoulli form); every edge whose
                               error bound (relative 2^-17 FP32, 2^-42 FP64) does not hold is
                               recomputed by the series kernels.  0 = default (6), -1 = never */
     int32_t range_check;   /* 1 = s3_sttsvc / s3_sttsvc_layout read the handle's range counter
