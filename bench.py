@@ -120,7 +120,7 @@ def bernoulli_flops(edges_per_size, N, sizes, form="product"):
 
 
 def hbm_bytes(nnz, n, esz=4, deterministic=True, comp=False):
-    """Algorithmic HBM bytes of one call by the survey's count: the int32 member ids
+    """Algorithmic HBM bytes of one call: the int32 member ids
     (4 per member), x gathered once and y written (esz per node each), the FP32
     compensation vector in atomic mode (4 per node), and, in deterministic mode, the
     per-(edge, node) buffer written by the edge kernels and read back by the reduce
